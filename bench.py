@@ -1,0 +1,448 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 vertex-reuse geometry stage.
+
+Workload: the large scanned-style mesh -- a class-I geodesic sphere of
+frequency 600 (3,600,002 vertices, 7,200,000 triangles), 2% radial noise,
+triangles in Morton (space-filling-curve) order with 5% of 256-triangle
+blocks shuffled, vertex ids randomly permuted, the MVP + normal shader.
+One step is one draw call of the whole mesh through the C ABI (indices,
+vertices and output resident in HBM); the headline variant is dynamic
+batching with hashing, its batch partition computed once at load time
+(Section 3.4) and timed separately.  Every reuse variant and the naive
+baseline are measured on the same mesh and reported under "variants".
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle (the
+plain definition of the result) on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import meshgen as mg  # noqa: E402
+
+FREQ = 600
+MESH_SEED = 2
+CAM_SEED = 2
+HEADLINE = "hash_dynamic"
+METRIC = "assembled triangles/s (vertex-reuse geometry stage, one draw of the 7.2M-triangle mesh)"
+UNIT = "triangles/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gp", choices=["gp", "reference"])
+    ap.add_argument("--variants", default="all", help="comma list of variant names, or 'all' / 'headline'")
+    ap.add_argument("--frequency", type=int, default=FREQ, help="geodesic frequency (600 = the benchmark mesh)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--clock-warm", type=float, default=1.0,
+                    help="seconds of headline draws before its warm-up, so the clock sampler sees the GPU under load")
+    return ap.parse_args()
+
+
+# (name, variant, mode, extra config)
+VARIANTS = [
+    ("naive", "naive", "static", {}),
+    ("warp_s96", "warp", "static", {"batch_indices": 96}),
+    ("sort_static_s768", "sort", "static", {"batch_indices": 768}),
+    ("hash_static_s768", "hash", "static", {"batch_indices": 768}),
+    ("phash_static_s768", "phash", "static", {"batch_indices": 768}),
+    ("sort_dynamic", "sort", "dynamic", {}),
+    ("hash_dynamic", "hash", "dynamic", {}),
+    ("phash_dynamic", "phash", "dynamic", {}),
+]
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def dram_traffic_record():
+    """ncu DRAM bytes per launch of the headline kernel, if the committed
+    profile summary matches the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        rec = json.load(open(p))
+    except Exception:
+        return None
+    import hashlib
+    src = os.path.join(ROOT, rec.get("source", ""))
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except Exception:
+        return None
+    if h != rec.get("source_sha256"):
+        return None
+    return rec
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        def reader():
+            for line in self.proc.stdout:
+                self.samples.append((time.time(), line.strip()))
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        rows = []
+        for ts, line in self.samples:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            rows.append((ts, parts))
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        inwin = [r for r in rows if t0 - 0.3 <= r[0] <= t1 + 0.3] or rows[-3:]
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(p[1]) for _, p in inwin if num(p[1]) is not None]
+        smax = [num(p[2]) for _, p in inwin if num(p[2]) is not None]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for _, p in inwin:
+            for name, val in zip(names, p[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(inwin),
+                "power_w_max": max((num(p[3]) or 0.0) for _, p in inwin)}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle legs
+# --------------------------------------------------------------------------
+
+CPU_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import meshgen as mg
+from oracle import shading as S
+mesh = mg.geodesic_sphere({freq}, {seed})
+M, N = mg.mvp_uniforms({cam})
+uni = {{"M": M, "N": N}}
+T = mesh.num_tris
+chunk = {chunk}
+budget = {budget}
+done = 0
+rng = np.random.default_rng(0)
+t0 = time.perf_counter()
+times = []
+while True:
+    start = int(rng.integers(0, max(1, T - chunk)))
+    s = time.perf_counter()
+    out = S.draw(mesh, S.SHADER_MVP, uni, tris=np.arange(start, min(T, start + chunk)))
+    times.append(time.perf_counter() - s)
+    done += out.shape[0]
+    if time.perf_counter() - t0 > budget and len(times) >= {min_steps}:
+        break
+el = sum(times)
+print(json.dumps({{"tris": done, "seconds": el, "steps": len(times), "per_step": times}}))
+"""
+
+
+def run_oracle(freq, chunk, budget, min_steps=1):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    code = CPU_SNIPPET.format(root=ROOT, freq=freq, seed=MESH_SEED, cam=CAM_SEED, chunk=chunk, budget=budget,
+                              min_steps=min_steps)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    chunk = 200_000
+    res = run_oracle(args.frequency, chunk, budget=0.0, min_steps=args.warmup + args.steps)
+    per = res["per_step"][args.warmup:args.warmup + args.steps]
+    tris = chunk * len(per)
+    secs = sum(per)
+    value = tris / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(per),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"geodesic sphere f={args.frequency} (7.2M triangles), MVP shader",
+                   "sample": f"{chunk} consecutive triangles per step at seeded random offsets"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{chunk} triangles per step, {len(per)} steps, float64 numpy oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    import paper_1805_08893_gb300 as gp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    t_gen = time.time()
+    mesh = mg.geodesic_sphere(args.frequency, MESH_SEED)
+    M, N = mg.mvp_uniforms(CAM_SEED)
+    uni = gp.uniforms_mvp(M, N)
+    gen_s = time.time() - t_gen
+    T, V = mesh.num_tris, mesh.num_vertices
+    idx = torch.from_numpy(mesh.indices.view(np.int32)).cuda()
+    verts = torch.from_numpy(mesh.vertices).cuda()
+    out = torch.empty(T * 21, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    ref_vertices = V  # every vertex of the mesh is referenced
+    algo_bytes = 12 * T + 32 * ref_vertices + 84 * T
+
+    names = [v[0] for v in VARIANTS]
+    if args.variants == "headline":
+        chosen = [HEADLINE]
+    elif args.variants == "all":
+        chosen = names
+    else:
+        chosen = [x for x in args.variants.split(",") if x in names]
+        if HEADLINE not in chosen:
+            chosen.append(HEADLINE)
+    # the headline runs last so that its timed region is the one sampled for clocks
+    chosen = [c for c in chosen if c != HEADLINE] + [HEADLINE]
+
+    results = {}
+    clocks = None
+    head = None
+    for name in chosen:
+        _, variant, mode, extra = next(v for v in VARIANTS if v[0] == name)
+        ctx = gp.gp_create(variant, mode=gp.GP_BATCH_DYNAMIC if mode == "dynamic" else gp.GP_BATCH_STATIC,
+                           stream=stream, **extra)
+        handle = 0
+        part_ms = None
+        nbatches = None
+        if mode == "dynamic":
+            # load-time partition (Section 3.4), timed on its own
+            ts = []
+            for rep in range(4):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h, _ = gp.gp_partition(ctx, idx, want_count=False)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+                if rep < 3:
+                    gp.gp_partition_release(ctx, h)
+                else:
+                    handle = h
+            part_ms = min(ts[1:])
+            nbatches = gp.gp_partition_starts(ctx, handle)
+        sampler = None
+        if name == HEADLINE:
+            sampler = ClockSampler(local)
+            sampler.start()
+            # keep the GPU busy ~1 s so the sampler sees the clocks under load
+            t_end = time.time() + args.clock_warm
+            while time.time() < t_end:
+                gp.gp_submit_drawcall(ctx, idx, verts, gp.GP_SHADER_MVP, uni, out, partition=handle)
+                gp.gp_sync(ctx)
+        for _ in range(args.warmup):
+            gp.gp_submit_drawcall(ctx, idx, verts, gp.GP_SHADER_MVP, uni, out, partition=handle)
+        gp.gp_sync(ctx)
+        gp.gp_stats(ctx, reset=True)
+        barrier()
+        w0 = time.time()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            gp.gp_submit_drawcall(ctx, idx, verts, gp.GP_SHADER_MVP, uni, out, partition=handle)
+        e1.record(stream)
+        barrier()
+        w1 = time.time()
+        ms_total = e0.elapsed_time(e1)
+        st = gp.gp_stats(ctx)
+        if sampler:
+            sampler.stop()
+            clocks = sampler.summary(w0, w1)
+        ms_step = ms_total / args.steps
+        if dist is not None:
+            tt = torch.tensor([ms_step], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ms_step = float(tt.item())
+        inv_per_draw = st["invocations"] / max(1, st["draws"])
+        kernel_ms = st["busy_ms"] / max(1, st["draws"])
+        results[name] = {
+            "triangles_per_s": world * T / (ms_step * 1e-3),
+            "ms_per_draw": ms_step,
+            "kernel_ms_mean": kernel_ms,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "invocations": int(inv_per_draw),
+            "shading_rate": inv_per_draw / ref_vertices,
+            "achieved_reuse": 1.0 - inv_per_draw / (3 * T),
+            "batches": int(st["batches"] / max(1, st["draws"])),
+            "hbm_gbs_algorithmic": algo_bytes / (kernel_ms * 1e-3) / 1e9,
+        }
+        if part_ms is not None:
+            results[name]["partition_ms"] = part_ms
+            results[name]["triangles_per_s_incl_partition"] = world * T / ((ms_step + part_ms) * 1e-3)
+            results[name]["dynamic_batches"] = nbatches
+        if name == HEADLINE:
+            head = (ctx, handle, kernel_ms, ms_step, st)
+        else:
+            if handle:
+                gp.gp_partition_release(ctx, handle)
+            gp.gp_destroy(ctx)
+        # keep the next variant's output from reusing stale values
+        torch.cuda.synchronize()
+
+    ctx, handle, kernel_ms, ms_step, st = head
+    naive_tps = results.get("naive", {}).get("triangles_per_s")
+
+    # end to end through the public API from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        hidx = torch.from_numpy(mesh.indices.view(np.int32)).pin_memory()
+        hvert = torch.from_numpy(mesh.vertices).pin_memory()
+        hout = torch.empty(T * 21, dtype=torch.float32).pin_memory()
+        ectx = gp.gp_create("hash", mode=gp.GP_BATCH_DYNAMIC, stream=stream)
+        ksteps = max(1, min(args.steps, 10))
+        for _ in range(2):
+            gp.gp_draw_host(ectx, hidx, hvert, gp.GP_SHADER_MVP, uni, hout)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ksteps):
+            gp.gp_draw_host(ectx, hidx, hvert, gp.GP_SHADER_MVP, uni, hout)
+        barrier()
+        el = (time.perf_counter() - t0) / ksteps
+        gp.gp_destroy(ectx)
+        e2e = {"value": world * T / el, "unit": UNIT, "h2d_bytes_per_step": int(hidx.numel() * 4 + hvert.numel() * 4),
+               "d2h_bytes_per_step": int(hout.numel() * 4), "ms_per_step": el * 1e3,
+               "note": "gp_draw_host: H2D of indices+vertices, dynamic partition, draw, D2H of all triangles"}
+
+    peak, peak_kind = load_peaks()
+    achieved = algo_bytes / (kernel_ms * 1e-3) / 1e9
+    traffic = dram_traffic_record()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_kind": f"of {peak_kind}", "traffic": traffic["bytes_per_launch"] if traffic else None,
+                "algorithmic_bytes_per_launch": algo_bytes,
+                "kernel": "batched_kernel<hash, mvp, dynamic>"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        chunk = 500_000
+        res = run_oracle(args.frequency, chunk, budget=10.0)
+        cpu = {"value": res["tris"] / res["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{res['steps']} x {chunk} consecutive triangles of the benchmark mesh at seeded "
+                         f"offsets, float64 numpy oracle (plain definition), one thread"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": world * T / (ms_step * 1e-3),
+            "unit": UNIT,
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms_step,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"large scanned-style mesh: geodesic sphere f={args.frequency}, "
+                                   f"{V} vertices / {T} triangles, Morton order + 5% block shuffle, "
+                                   f"permuted vertex ids, MVP+normal shader",
+                       "variant": HEADLINE, "max_unique": 256, "max_tris": 341, "threads_per_group": 256,
+                       "segment_tris": 4096, "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs (201 MB) and output (605 MB) exceed the 126 MB L2; no flush"},
+            "shading_rate": results[HEADLINE]["shading_rate"],
+            "p99_draw_ms": st["p99_ms"],
+            "vs_naive": (results[HEADLINE]["triangles_per_s"] / naive_tps) if naive_tps else None,
+            "partition_ms": results[HEADLINE].get("partition_ms"),
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "variants": results,
+            "mesh_gen_s": gen_s,
+        }
+        print(json.dumps(line))
+    if handle:
+        gp.gp_partition_release(ctx, handle)
+    gp.gp_destroy(ctx)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

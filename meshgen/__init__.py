@@ -10,7 +10,7 @@ available (Section 4, Table 1).  The generators below stand in for them with
 the statistics that matter to vertex reuse (Section 4.1, Table 1): a closed
 mesh with V/T = 1/2 (ideal reuse 5/6, like the bunny, sphere, buddha and
 dragon rows), triangles in a locality order (the paper reorders every model
-with a cache optimiser, Section 3.5), and vertex ids with no relation to
+with a cache optimiser, Section 4), and vertex ids with no relation to
 position.
 
 Vertex layouts (little endian, one row per vertex):
@@ -267,9 +267,9 @@ def geodesic_sphere(f: int, seed: int, noise: float = 0.02, block: int = 256,
 
     * radius 1 + noise * u_v, u_v ~ U[-1, 1] per vertex;
     * area-weighted normals in float64, rounded to float32;
-    * triangles sorted by the Morton code of their centroid, then a fraction
-      ``shuffle_frac`` of the full ``block``-triangle blocks permuted among
-      themselves (locality order with local disorder);
+    * triangles sorted by the Morton code of their centroid on the noise-free
+      sphere, then a fraction ``shuffle_frac`` of the full ``block``-triangle
+      blocks permuted among themselves (locality order with local disorder);
     * vertex ids randomly permuted, so an id says nothing about position.
     """
     rng = np.random.default_rng(seed)
@@ -279,7 +279,10 @@ def geodesic_sphere(f: int, seed: int, noise: float = 0.02, block: int = 256,
     pos = dirs * radius[:, None]
     nrm = vertex_normals(pos, tris)
     if order == "morton":
-        cent = (pos[tris[:, 0]] + pos[tris[:, 1]] + pos[tris[:, 2]]) / 3.0
+        # the locality order is taken on the noise-free sphere: at high
+        # frequency the 2% radial noise is many edge lengths, and ordering the
+        # noisy centroids would scatter neighbouring triangles
+        cent = (dirs[tris[:, 0]] + dirs[tris[:, 1]] + dirs[tris[:, 2]]) / 3.0
         tris = tris[morton_order(cent)]
         nb = tris.shape[0] // block
         m = int(round(shuffle_frac * nb))

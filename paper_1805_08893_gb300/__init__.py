@@ -1,0 +1,327 @@
+"""Python binding of the GB300 vertex-reuse geometry stage (libgp.so).
+
+Argument marshalling only: every step of the geometry stage runs in the CUDA
+kernels behind the C ABI declared in ``include/gp.h``.  The functions keep the
+C names (``gp_create``, ``gp_submit_drawcall``, ``gp_sync``, ...).  Device
+buffers are torch CUDA tensors (PyTorch provides memory and streams); there is
+no CPU fallback: if the library cannot be loaded, importing this package
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "GpError", "gp_create", "gp_destroy", "gp_partition", "gp_partition_starts", "gp_partition_release",
+    "gp_submit_drawcall", "gp_sync", "gp_stats", "gp_draw_host", "gp_out_floats", "gp_static_batch_count",
+    "gp_last_error", "gp_status_string", "uniforms_mvp", "uniforms_skin", "uniforms_envelope", "uniforms_load",
+    "Context", "lib", "library_path",
+]
+
+# enums (gp.h)
+GP_OK, GP_ERR_INVALID, GP_ERR_OOM, GP_ERR_CUDA, GP_ERR_TIMEOUT, GP_ERR_BUSY, GP_ERR_INDEX_RANGE, \
+    GP_ERR_UNSUPPORTED = range(8)
+GP_NAIVE, GP_WARP, GP_SORT, GP_HASH, GP_PHASH, GP_AUTO = range(6)
+GP_BATCH_STATIC, GP_BATCH_DYNAMIC = 0, 1
+GP_SHADER_MVP, GP_SHADER_SKIN, GP_SHADER_ENVELOPE, GP_SHADER_LOAD = range(4)
+GP_VFMT_PNU32, GP_VFMT_SKIN64 = 0, 1
+GP_SEGMENT_NONE = 0xFFFFFFFF
+
+VARIANTS = {"naive": GP_NAIVE, "warp": GP_WARP, "sort": GP_SORT, "hash": GP_HASH, "phash": GP_PHASH}
+
+
+class gp_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("variant", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("batch_indices", ctypes.c_uint32), ("max_unique", ctypes.c_uint32),
+                ("max_tris", ctypes.c_uint32), ("threads_per_group", ctypes.c_uint32),
+                ("probe_k", ctypes.c_uint32), ("hash_slots", ctypes.c_uint32),
+                ("segment_tris", ctypes.c_uint32), ("flags", ctypes.c_uint32),
+                ("mem_budget_bytes", ctypes.c_uint64), ("stream", ctypes.c_void_p)]
+
+
+class gp_index_buf(ctypes.Structure):
+    _fields_ = [("d_indices", ctypes.c_void_p), ("num_indices", ctypes.c_uint64), ("partition", ctypes.c_uint64)]
+
+
+class gp_vertex_buf(ctypes.Structure):
+    _fields_ = [("d_vertices", ctypes.c_void_p), ("num_vertices", ctypes.c_uint64),
+                ("stride_bytes", ctypes.c_uint32), ("format", ctypes.c_uint32)]
+
+
+class gp_out_buf(ctypes.Structure):
+    _fields_ = [("d_out", ctypes.c_void_p), ("capacity_bytes", ctypes.c_uint64),
+                ("d_corner_ids", ctypes.c_void_p), ("d_batch_invocations", ctypes.c_void_p),
+                ("batch_capacity", ctypes.c_uint64)]
+
+
+class gp_uniforms_mvp(ctypes.Structure):
+    _fields_ = [("mvp", ctypes.c_float * 16), ("normal", ctypes.c_float * 9)]
+
+
+class gp_uniforms_skin(ctypes.Structure):
+    _fields_ = [("mvp", ctypes.c_float * 16), ("normal", ctypes.c_float * 9), ("palette", ctypes.c_float * 768)]
+
+
+class gp_uniforms_envelope(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_float), ("num_dirs", ctypes.c_uint32), ("dirs", ctypes.c_float * 48)]
+
+
+class gp_uniforms_load(ctypes.Structure):
+    _fields_ = [("mvp", ctypes.c_float * 16), ("normal", ctypes.c_float * 9), ("steps", ctypes.c_uint32)]
+
+
+class gp_stats_t(ctypes.Structure):
+    _fields_ = [("draws", ctypes.c_uint64), ("triangles", ctypes.c_uint64), ("indices", ctypes.c_uint64),
+                ("invocations", ctypes.c_uint64), ("batches", ctypes.c_uint64), ("busy_ms", ctypes.c_double),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("bytes_moved", ctypes.c_uint64),
+                ("last_error", ctypes.c_uint32)]
+
+
+class GpError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(message)
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path) or os.environ.get("GP_BUILD_ON_IMPORT", "1") == "1":
+        _build.build()
+    L = ctypes.CDLL(path)
+    P, U64, U32, I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+    sig = {
+        "gp_create": ([ctypes.POINTER(gp_config), ctypes.POINTER(P)], I),
+        "gp_destroy": ([P], I),
+        "gp_partition": ([P, ctypes.POINTER(gp_index_buf), ctypes.POINTER(U64), ctypes.POINTER(U64)], I),
+        "gp_partition_starts": ([P, U64, P, U64, ctypes.POINTER(U64)], I),
+        "gp_partition_release": ([P, U64], I),
+        "gp_submit_drawcall": ([P, ctypes.POINTER(gp_index_buf), ctypes.POINTER(gp_vertex_buf), U32, P, U32,
+                                ctypes.POINTER(gp_out_buf), ctypes.POINTER(U64)], I),
+        "gp_sync": ([P, U64, U32], I),
+        "gp_stats": ([P, ctypes.POINTER(gp_stats_t), I], I),
+        "gp_draw_host": ([P, P, U64, P, U64, U32, U32, U32, P, U32, P, U64], I),
+        "gp_out_floats": ([U32], U32),
+        "gp_static_batch_count": ([P, U64], U64),
+        "gp_last_error": ([P], ctypes.c_char_p),
+        "gp_status_string": ([I], ctypes.c_char_p),
+    }
+    for name, (argt, rest) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = argt
+        f.restype = rest
+    return L
+
+
+lib = _load()
+
+
+def gp_last_error(ctx=None) -> str:
+    return lib.gp_last_error(ctx).decode()
+
+
+def gp_status_string(status: int) -> str:
+    return lib.gp_status_string(status).decode()
+
+
+def _check(status: int, ctx=None):
+    if status != GP_OK:
+        raise GpError(status, gp_last_error(ctx) or gp_status_string(status))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def gp_create(variant="hash", mode=GP_BATCH_STATIC, device=0, batch_indices=0, max_unique=0, max_tris=0,
+              threads_per_group=0, probe_k=0, hash_slots=0, segment_tris=0, mem_budget_bytes=0, stream=None):
+    """gp_create: returns an opaque context handle."""
+    cfg = gp_config(device, VARIANTS.get(variant, variant), int(mode), batch_indices, max_unique, max_tris,
+                    threads_per_group, probe_k, hash_slots, segment_tris, 0, mem_budget_bytes,
+                    _stream_handle(stream))
+    h = ctypes.c_void_p()
+    _check(lib.gp_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def gp_destroy(ctx):
+    _check(lib.gp_destroy(ctx))
+
+
+def _index_buf(indices, partition=0):
+    assert indices.is_cuda and indices.is_contiguous() and indices.element_size() == 4
+    return gp_index_buf(indices.data_ptr(), indices.numel(), partition)
+
+
+def gp_partition(ctx, indices, want_count=True):
+    """gp_partition: returns (handle, number of batches or None)."""
+    ib = _index_buf(indices)
+    h = ctypes.c_uint64()
+    n = ctypes.c_uint64()
+    _check(lib.gp_partition(ctx, ctypes.byref(ib), ctypes.byref(h), ctypes.byref(n) if want_count else None), ctx)
+    return h.value, (n.value if want_count else None)
+
+
+def gp_partition_starts(ctx, handle, out=None):
+    """gp_partition_starts: copies the starts into ``out`` (uint32/int32 CUDA
+    tensor) if given; returns the number of batches."""
+    n = ctypes.c_uint64()
+    cap = 0 if out is None else out.numel()
+    _check(lib.gp_partition_starts(ctx, handle, _ptr(out), cap, ctypes.byref(n)), ctx)
+    return n.value
+
+
+def gp_partition_release(ctx, handle):
+    _check(lib.gp_partition_release(ctx, handle), ctx)
+
+
+def _vertex_buf(vertices, num_vertices=None, fmt=None):
+    assert vertices.is_cuda and vertices.is_contiguous() and vertices.dim() == 2
+    stride = vertices.shape[1] * vertices.element_size()
+    if fmt is None:
+        fmt = GP_VFMT_SKIN64 if stride == 64 else GP_VFMT_PNU32
+    nv = vertices.shape[0] if num_vertices is None else num_vertices
+    return gp_vertex_buf(vertices.data_ptr(), nv, stride, fmt)
+
+
+def gp_submit_drawcall(ctx, indices, vertices, shader_id, uniforms, out, corner_ids=None, batch_invocations=None,
+                       partition=0, num_vertices=None, fmt=None):
+    """gp_submit_drawcall: returns the ticket.  ``uniforms`` is one of the
+    gp_uniforms_* ctypes structures."""
+    ib = _index_buf(indices, partition)
+    vb = _vertex_buf(vertices, num_vertices, fmt)
+    ob = gp_out_buf(out.data_ptr(), out.numel() * out.element_size(),
+                    None if corner_ids is None else corner_ids.data_ptr(),
+                    None if batch_invocations is None else batch_invocations.data_ptr(),
+                    0 if batch_invocations is None else batch_invocations.numel())
+    t = ctypes.c_uint64()
+    _check(lib.gp_submit_drawcall(ctx, ctypes.byref(ib), ctypes.byref(vb), shader_id,
+                                  ctypes.cast(ctypes.byref(uniforms), ctypes.c_void_p), ctypes.sizeof(uniforms),
+                                  ctypes.byref(ob), ctypes.byref(t)), ctx)
+    return t.value
+
+
+def gp_sync(ctx, ticket=0, timeout_ms=0, raise_on_error=True):
+    """gp_sync: returns the status (raises GpError on a non-OK status unless
+    ``raise_on_error`` is False)."""
+    s = lib.gp_sync(ctx, ticket, timeout_ms)
+    if raise_on_error:
+        _check(s, ctx)
+    return s
+
+
+def gp_stats(ctx, reset=False) -> dict:
+    st = gp_stats_t()
+    _check(lib.gp_stats(ctx, ctypes.byref(st), 1 if reset else 0), ctx)
+    return {name: getattr(st, name) for name, _ in gp_stats_t._fields_}
+
+
+def gp_draw_host(ctx, indices, vertices, shader_id, uniforms, out, fmt=None):
+    """gp_draw_host: end-to-end draw from host memory (numpy arrays or CPU
+    tensors, ideally pinned).  ``out`` receives the triangles."""
+    def addr(x):
+        return x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr()
+
+    def nbytes(x):
+        return x.nbytes if isinstance(x, np.ndarray) else x.numel() * x.element_size()
+    nidx = indices.size if isinstance(indices, np.ndarray) else indices.numel()
+    nv = vertices.shape[0]
+    stride = nbytes(vertices) // max(nv, 1)
+    if fmt is None:
+        fmt = GP_VFMT_SKIN64 if stride == 64 else GP_VFMT_PNU32
+    s = lib.gp_draw_host(ctx, addr(indices), nidx, addr(vertices), nv, stride, fmt, shader_id,
+                         ctypes.cast(ctypes.byref(uniforms), ctypes.c_void_p), ctypes.sizeof(uniforms),
+                         addr(out), nbytes(out))
+    _check(s, ctx)
+
+
+def gp_out_floats(shader_id: int) -> int:
+    return lib.gp_out_floats(shader_id)
+
+
+def gp_static_batch_count(ctx, num_indices: int) -> int:
+    return lib.gp_static_batch_count(ctx, num_indices)
+
+
+# ---------------------------------------------------------------------------
+# uniform blobs
+# ---------------------------------------------------------------------------
+
+def _fill(arr, values):
+    v = np.ascontiguousarray(np.asarray(values, dtype=np.float32).reshape(-1))
+    assert v.size == len(arr), (v.size, len(arr))
+    ctypes.memmove(arr, v.ctypes.data, v.nbytes)
+
+
+def uniforms_mvp(M, N) -> gp_uniforms_mvp:
+    u = gp_uniforms_mvp()
+    _fill(u.mvp, M)
+    _fill(u.normal, N)
+    return u
+
+
+def uniforms_skin(M, N, palette) -> gp_uniforms_skin:
+    u = gp_uniforms_skin()
+    _fill(u.mvp, M)
+    _fill(u.normal, N)
+    _fill(u.palette, palette)
+    return u
+
+
+def uniforms_envelope(d, dirs) -> gp_uniforms_envelope:
+    u = gp_uniforms_envelope()
+    dirs = np.asarray(dirs, dtype=np.float32).reshape(-1, 3)
+    u.d = float(d)
+    u.num_dirs = dirs.shape[0]
+    full = np.zeros((16, 3), np.float32)
+    full[: dirs.shape[0]] = dirs
+    _fill(u.dirs, full)
+    return u
+
+
+def uniforms_load(M, N, steps) -> gp_uniforms_load:
+    u = gp_uniforms_load()
+    _fill(u.mvp, M)
+    _fill(u.normal, N)
+    u.steps = int(steps)
+    return u
+
+
+class Context:
+    """Owns a gp_ctx handle (``with Context(...) as c:``)."""
+
+    def __init__(self, variant="hash", **kw):
+        self.handle = gp_create(variant, **kw)
+
+    def close(self):
+        if self.handle:
+            gp_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,798 @@
+// C-ABI runtime of the geometry stage: contexts, argument checking, kernel
+// selection and sizing, tickets, partitions and statistics.  Every compute
+// step runs in the kernels of gp_draw_*.cu and gp_partition.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <cstdio>
+#include <cstdlib>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "gp.h"
+#include "gp_internal.h"
+
+using namespace gp;
+
+namespace {
+
+constexpr uint32_t kRing = 1024;   // in-flight draws with their own device record
+
+struct alignas(128) DevRec {
+  uint32_t err;
+  uint32_t pad;
+  unsigned long long cnt[15];
+};
+static_assert(sizeof(DevRec) == 128, "device record layout");
+
+struct Ticket {
+  uint64_t id = 0;
+  uint32_t slot = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  uint64_t tris = 0, indices = 0;
+  uint64_t host_inv = 0, host_batches = 0;  // counts known on the host (naive)
+  bool device_counts = false;
+  uint64_t out_bytes = 0;
+  uint32_t stride = 0;
+};
+
+struct Partition {
+  const uint32_t* idx = nullptr;
+  uint64_t num_idx = 0;
+  uint32_t* d_starts = nullptr;  // count + 1 entries
+  uint32_t* d_count = nullptr;
+  uint32_t* d_seg = nullptr;     // seg_starts, then seg_counts (2 x nseg)
+  uint32_t max_batches = 0;
+  uint32_t num_segments = 0, seg_cap = 0;
+  uint32_t max_unique = 0, max_tris = 0, segment_tris = 0;
+  cudaEvent_t done = nullptr;
+  bool count_known = false;
+  uint64_t count = 0;
+};
+
+uint32_t next_pow2(uint32_t x) {
+  uint32_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+uint32_t log2u(uint32_t x) {
+  uint32_t b = 0;
+  while ((1u << b) < x) ++b;
+  return b;
+}
+
+const char* status_name(gp_status s) {
+  switch (s) {
+    case GP_OK: return "GP_OK";
+    case GP_ERR_INVALID: return "GP_ERR_INVALID";
+    case GP_ERR_OOM: return "GP_ERR_OOM";
+    case GP_ERR_CUDA: return "GP_ERR_CUDA";
+    case GP_ERR_TIMEOUT: return "GP_ERR_TIMEOUT";
+    case GP_ERR_BUSY: return "GP_ERR_BUSY";
+    case GP_ERR_INDEX_RANGE: return "GP_ERR_INDEX_RANGE";
+    case GP_ERR_UNSUPPORTED: return "GP_ERR_UNSUPPORTED";
+  }
+  return "GP_ERR_UNKNOWN";
+}
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct gp_ctx {
+  std::mutex mu;
+  gp_config cfg{};
+  cudaStream_t stream = nullptr;
+  cudaStream_t aux = nullptr;
+  int device = 0;
+  int sms = 0;
+  DevRec* d_rec = nullptr;
+  DevRec* h_rec = nullptr;  // pinned mirror
+  std::deque<Ticket> inflight;
+  uint64_t next_ticket = 1;
+  std::vector<cudaEvent_t> events;
+  std::unordered_map<uint64_t, Partition> parts;
+  uint64_t next_part = 1;
+  Partition temp_part;  // submit-time partition scratch (dynamic draw without a handle)
+  // statistics of folded draws
+  uint64_t s_draws = 0, s_tris = 0, s_idx = 0, s_inv = 0, s_batches = 0, s_bytes = 0;
+  double s_busy = 0.0;
+  std::vector<float> s_lat;
+  // errors
+  gp_status last_status = GP_OK;
+  std::string last_error;
+  // host-draw staging
+  void* h_idx = nullptr;
+  size_t h_idx_cap = 0;
+  void* h_vtx = nullptr;
+  size_t h_vtx_cap = 0;
+  void* h_out = nullptr;
+  size_t h_out_cap = 0;
+  // occupancy cache: key -> blocks per SM
+  std::unordered_map<uint64_t, int> occ;
+  std::unordered_set<uint64_t> logged;
+};
+
+namespace {
+
+gp_status fail(gp_ctx* c, gp_status s, const std::string& msg) {
+  if (c) {
+    c->last_status = s;
+    c->last_error = std::string(status_name(s)) + ": " + msg;
+  } else {
+    g_create_error = std::string(status_name(s)) + ": " + msg;
+  }
+  return s;
+}
+
+gp_status cuda_fail(gp_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, e == cudaErrorMemoryAllocation ? GP_ERR_OOM : GP_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define GP_CUDA(ctx, call)                                   \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+cudaEvent_t get_event(gp_ctx* c) {
+  if (!c->events.empty()) {
+    cudaEvent_t e = c->events.back();
+    c->events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+void put_event(gp_ctx* c, cudaEvent_t e) {
+  if (e) c->events.push_back(e);
+}
+
+void release_partition(Partition& p) {
+  if (p.d_starts) cudaFree(p.d_starts);
+  if (p.d_seg) cudaFree(p.d_seg);
+  if (p.done) cudaEventDestroy(p.done);
+  p = Partition{};
+}
+
+// Wait for an event with an optional limit (ms; 0 = none).
+gp_status wait_event(gp_ctx* c, cudaEvent_t e, uint32_t timeout_ms) {
+  if (timeout_ms == 0) {
+    GP_CUDA(c, cudaEventSynchronize(e));
+    return GP_OK;
+  }
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    cudaError_t q = cudaEventQuery(e);
+    if (q == cudaSuccess) return GP_OK;
+    if (q != cudaErrorNotReady) return cuda_fail(c, q, "cudaEventQuery");
+    const auto ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (ms > timeout_ms) return fail(c, GP_ERR_TIMEOUT, "draw did not complete in time");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+// Folds completed tickets (front of the queue, up to and including 'upto')
+// into the statistics.  Their events must have completed.
+gp_status fold(gp_ctx* c, uint64_t upto) {
+  gp_status worst = GP_OK;
+  if (c->inflight.empty() || c->inflight.front().id > upto) return GP_OK;
+  // the records of the folded tickets are consecutive ring slots (maybe wrapping)
+  {
+    const uint32_t first = c->inflight.front().slot;
+    uint64_t n = 0;
+    for (const Ticket& t : c->inflight)
+      if (t.id <= upto) ++n;
+    const uint32_t run1 = (uint32_t)std::min<uint64_t>(n, kRing - first);
+    GP_CUDA(c, cudaMemcpyAsync(c->h_rec + first, c->d_rec + first, sizeof(DevRec) * run1, cudaMemcpyDeviceToHost,
+                               c->aux));
+    if (n > run1)
+      GP_CUDA(c, cudaMemcpyAsync(c->h_rec, c->d_rec, sizeof(DevRec) * (n - run1), cudaMemcpyDeviceToHost, c->aux));
+    GP_CUDA(c, cudaMemcpyAsync(c->h_rec + kRing, c->d_rec + kRing, sizeof(DevRec), cudaMemcpyDeviceToHost, c->aux));
+    GP_CUDA(c, cudaStreamSynchronize(c->aux));
+    if (c->h_rec[kRing].err) worst = fail(c, GP_ERR_UNSUPPORTED, "the dynamic partition exceeded a capacity");
+  }
+  while (!c->inflight.empty() && c->inflight.front().id <= upto) {
+    Ticket t = c->inflight.front();
+    c->inflight.pop_front();
+    const DevRec& r = c->h_rec[t.slot];
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t.ev0, t.ev1);
+    put_event(c, t.ev0);
+    put_event(c, t.ev1);
+    const uint64_t inv = t.device_counts ? r.cnt[CNT_INVOCATIONS] : t.host_inv;
+    const uint64_t bat = t.device_counts ? r.cnt[CNT_BATCHES] : t.host_batches;
+    c->s_draws += 1;
+    c->s_tris += t.tris;
+    c->s_idx += t.indices;
+    c->s_inv += inv;
+    c->s_batches += bat;
+    c->s_bytes += 4 * t.indices + (uint64_t)t.stride * inv + t.out_bytes;
+    c->s_busy += ms;
+    c->s_lat.push_back(ms);
+    gp_status s = GP_OK;
+    if (r.err & EBIT_TIMEOUT) s = fail(c, GP_ERR_TIMEOUT, "a bounded device wait gave up");
+    else if (r.err & EBIT_CAPACITY) s = fail(c, GP_ERR_UNSUPPORTED, "a batch exceeded a shared-memory capacity");
+    else if (r.err & EBIT_INDEX_RANGE) s = fail(c, GP_ERR_INDEX_RANGE, "index >= num_vertices in a draw");
+    if (worst == GP_OK) worst = s;
+  }
+  return worst;
+}
+
+gp_status sync_locked(gp_ctx* c, uint64_t ticket, uint32_t timeout_ms) {
+  if (c->inflight.empty()) return GP_OK;
+  if (ticket == 0) ticket = c->inflight.back().id;
+  // the newest ticket <= 'ticket'
+  const Ticket* last = nullptr;
+  for (const Ticket& t : c->inflight)
+    if (t.id <= ticket) last = &t;
+  if (!last) return GP_OK;  // already folded
+  gp_status s = wait_event(c, last->ev1, timeout_ms);
+  if (s != GP_OK) return s;
+  return fold(c, last->id);
+}
+
+uint32_t default_batch(const gp_config& cfg) {
+  if (cfg.batch_indices) return cfg.batch_indices;
+  switch (cfg.variant) {
+    case GP_WARP: return 96;
+    case GP_NAIVE: return 3 * (cfg.threads_per_group ? cfg.threads_per_group : 256);
+    default: return 768;
+  }
+}
+
+gp_status make_uniforms(gp_ctx* c, uint32_t shader, const void* blob, uint32_t bytes, Uniforms& u) {
+  std::memset(&u, 0, sizeof(u));
+  if (!blob) return fail(c, GP_ERR_INVALID, "uniforms is NULL");
+  switch (shader) {
+    case GP_SHADER_MVP: {
+      if (bytes != sizeof(gp_uniforms_mvp)) return fail(c, GP_ERR_INVALID, "uniforms_bytes != sizeof(gp_uniforms_mvp)");
+      const gp_uniforms_mvp* m = static_cast<const gp_uniforms_mvp*>(blob);
+      std::memcpy(u.mvp, m->mvp, sizeof(u.mvp));
+      std::memcpy(u.nrm, m->normal, sizeof(u.nrm));
+      return GP_OK;
+    }
+    case GP_SHADER_SKIN: {
+      if (bytes != sizeof(gp_uniforms_skin)) return fail(c, GP_ERR_INVALID, "uniforms_bytes != sizeof(gp_uniforms_skin)");
+      const gp_uniforms_skin* m = static_cast<const gp_uniforms_skin*>(blob);
+      std::memcpy(u.mvp, m->mvp, sizeof(u.mvp));
+      std::memcpy(u.nrm, m->normal, sizeof(u.nrm));
+      std::memcpy(u.palette, m->palette, sizeof(u.palette));
+      return GP_OK;
+    }
+    case GP_SHADER_ENVELOPE: {
+      if (bytes != sizeof(gp_uniforms_envelope))
+        return fail(c, GP_ERR_INVALID, "uniforms_bytes != sizeof(gp_uniforms_envelope)");
+      const gp_uniforms_envelope* m = static_cast<const gp_uniforms_envelope*>(blob);
+      if (m->num_dirs < 1 || m->num_dirs > (uint32_t)kMaxEnvelopeDirs)
+        return fail(c, GP_ERR_INVALID, "envelope num_dirs must be in 1..16");
+      u.d = m->d;
+      u.num_dirs = m->num_dirs;
+      u.inv_dirs = (float)(1.0 / (double)m->num_dirs);
+      std::memcpy(u.dirs, m->dirs, sizeof(u.dirs));
+      double f = 1.0;  // k!
+      for (int k = 0; k < kEnvelopeTerms; ++k) {
+        if (k > 0) f *= (double)k;
+        u.coef[k] = (float)(1.0 / f);
+      }
+      return GP_OK;
+    }
+    case GP_SHADER_LOAD: {
+      if (bytes != sizeof(gp_uniforms_load)) return fail(c, GP_ERR_INVALID, "uniforms_bytes != sizeof(gp_uniforms_load)");
+      const gp_uniforms_load* m = static_cast<const gp_uniforms_load*>(blob);
+      std::memcpy(u.mvp, m->mvp, sizeof(u.mvp));
+      std::memcpy(u.nrm, m->normal, sizeof(u.nrm));
+      u.steps = m->steps;
+      return GP_OK;
+    }
+  }
+  return fail(c, GP_ERR_INVALID, "unknown shader_id");
+}
+
+// Enqueues the partition kernels for 'p' (already sized) on the stream.
+gp_status run_partition(gp_ctx* c, Partition& p, const uint32_t* idx, uint64_t num_idx) {
+  PartitionArgs a{};
+  a.idx = idx;
+  a.num_tris = (uint32_t)(num_idx / 3);
+  a.max_unique = p.max_unique;
+  a.max_tris = p.max_tris;
+  a.segment_tris = p.segment_tris;
+  a.num_segments = p.num_segments;
+  a.seg_cap = p.seg_cap;
+  a.table_slots = next_pow2(2 * (p.max_unique + 96));
+  a.table_bits = log2u(a.table_slots);
+  a.seg_starts = p.d_seg;
+  a.seg_counts = p.d_seg + (size_t)p.num_segments * p.seg_cap;
+  a.starts = p.d_starts;
+  a.num_batches = p.d_count;
+  a.err = &c->d_rec[kRing].err;  // the record after the draw ring collects partition errors
+  GP_CUDA(c, launch_partition(a, 4, c->stream));
+  return GP_OK;
+}
+
+// Sizes (and allocates if needed) a partition for num_idx indices.
+gp_status size_partition(gp_ctx* c, Partition& p, uint64_t num_idx, bool reuse_alloc) {
+  const uint32_t T = (uint32_t)(num_idx / 3);
+  const uint32_t nu = c->cfg.max_unique, mt = c->cfg.max_tris;
+  const uint32_t seg = c->cfg.segment_tris == GP_SEGMENT_NONE ? std::max(T, 1u) : c->cfg.segment_tris;
+  const uint32_t min_tris = std::max(1u, std::min(mt, (nu - 2 + 2) / 3));
+  const uint32_t nseg = T ? (T + seg - 1) / seg : 0;
+  const uint32_t seg_cap = (std::min(seg, std::max(T, 1u)) + min_tris - 1) / min_tris + 1;
+  const uint64_t max_b = (uint64_t)nseg * seg_cap;
+  const size_t need_seg = ((size_t)nseg * seg_cap + 2 * (size_t)nseg + 1) * 4;
+  const size_t need_starts = (max_b + 2) * 4;
+  const bool fits = reuse_alloc && p.d_starts && p.max_batches >= max_b &&
+                    (size_t)p.num_segments * p.seg_cap + 2 * (size_t)p.num_segments + 1 >= need_seg / 4;
+  if (!fits) {
+    if (p.d_starts) cudaFree(p.d_starts);
+    if (p.d_seg) cudaFree(p.d_seg);
+    p.d_starts = nullptr;
+    p.d_seg = nullptr;
+    void* ptr = nullptr;
+    GP_CUDA(c, cudaMalloc(&ptr, need_starts + 16));
+    p.d_starts = static_cast<uint32_t*>(ptr);
+    GP_CUDA(c, cudaMalloc(&ptr, need_seg + 16));
+    p.d_seg = static_cast<uint32_t*>(ptr);
+    p.max_batches = (uint32_t)max_b;
+  }
+  p.d_count = p.d_starts + max_b + 1;
+  p.num_segments = nseg;
+  p.seg_cap = seg_cap;
+  p.max_unique = nu;
+  p.max_tris = mt;
+  p.segment_tris = seg;
+  p.num_idx = num_idx;
+  return GP_OK;
+}
+
+gp_status check_index_buf(gp_ctx* c, const gp_index_buf* ib) {
+  if (!ib) return fail(c, GP_ERR_INVALID, "index_buf is NULL");
+  if (ib->num_indices % 3) return fail(c, GP_ERR_INVALID, "num_indices is not a multiple of 3");
+  if (ib->num_indices >= 0xFFFFFFF0ull) return fail(c, GP_ERR_INVALID, "num_indices must be < 2^32 - 16");
+  if (ib->num_indices && !ib->d_indices) return fail(c, GP_ERR_INVALID, "d_indices is NULL");
+  if (reinterpret_cast<uintptr_t>(ib->d_indices) % 16)
+    return fail(c, GP_ERR_INVALID, "d_indices must be 16-byte aligned");
+  return GP_OK;
+}
+
+// Enqueues one draw (after validation); fills the ticket's counters.
+gp_status enqueue_draw(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* vb, uint32_t shader,
+                       const Uniforms& u, const gp_out_buf* ob, Ticket& t, DevRec* rec) {
+  const gp_config& cfg = c->cfg;
+  const uint32_t T = (uint32_t)(ib->num_indices / 3);
+  DrawArgs a{};
+  a.idx = ib->d_indices;
+  a.num_idx = (uint32_t)ib->num_indices;
+  a.num_tris = T;
+  a.verts = static_cast<const unsigned char*>(vb->d_vertices);
+  a.num_verts = (uint32_t)vb->num_vertices;
+  a.stride = vb->stride_bytes;
+  a.out = ob->d_out;
+  a.corner_ids = ob->d_corner_ids;
+  a.batch_inv = ob->d_batch_invocations;
+  a.batch_cap = (uint32_t)std::min<uint64_t>(ob->batch_capacity, 0xFFFFFFFFu);
+  a.counters = rec->cnt;
+  a.err = &rec->err;
+  a.probe_k = cfg.probe_k;
+  t.tris = T;
+  t.indices = ib->num_indices;
+  t.stride = vb->stride_bytes;
+  t.out_bytes = (uint64_t)T * 3 * out_floats((int)shader) * 4;
+  if (T == 0) return GP_OK;
+  const uint32_t threads = cfg.threads_per_group;
+
+  if (cfg.variant == GP_NAIVE) {
+    const int block = threads;
+    t.host_inv = 3ull * T;
+    t.host_batches = (T + block - 1) / block;
+    GP_CUDA(c, launch_naive(a, u, (int)shader, block, c->stream));
+    return GP_OK;
+  }
+  if (cfg.variant == GP_WARP) {
+    const uint32_t S = default_batch(cfg);
+    a.static_batch_tris = S / 3;
+    a.num_batches = (T + a.static_batch_tris - 1) / a.static_batch_tris;
+    const int wpb = std::max(1u, threads / 32);
+    const uint64_t key = (1ull << 40) | ((uint64_t)shader << 32) | (uint64_t)wpb;
+    auto it = c->occ.find(key);
+    const int bpsm = it != c->occ.end() ? it->second : (c->occ[key] = warp_kernel_blocks_per_sm((int)shader, wpb));
+    const uint64_t want = ((uint64_t)a.num_batches + wpb - 1) / wpb;
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)c->sms * bpsm, want));
+    if (std::getenv("GP_VERBOSE") && c->logged.insert(key).second)
+      std::fprintf(stderr, "[gp] warp shader=%u warps/block=%d blocks/SM=%d grid=%d batch=%u\n", shader, wpb, bpsm,
+                   grid, S);
+    t.device_counts = true;
+    GP_CUDA(c, launch_warp(a, u, (int)shader, wpb, grid, c->stream));
+    return GP_OK;
+  }
+  // sort / hash / phash
+  const int dedup = cfg.variant == GP_SORT ? DEDUP_SORT : (cfg.variant == GP_HASH ? DEDUP_HASH : DEDUP_PHASH);
+  const bool dyn = cfg.mode == GP_BATCH_DYNAMIC;
+  if (dyn) {
+    Partition* p = nullptr;
+    if (ib->partition) {
+      auto it = c->parts.find(ib->partition);
+      if (it == c->parts.end()) return fail(c, GP_ERR_INVALID, "unknown partition handle");
+      p = &it->second;
+      if (p->idx != ib->d_indices || p->num_idx != ib->num_indices)
+        return fail(c, GP_ERR_INVALID, "partition handle belongs to another index buffer");
+    } else {
+      p = &c->temp_part;
+      gp_status s = size_partition(c, *p, ib->num_indices, true);
+      if (s != GP_OK) return s;
+      p->idx = ib->d_indices;
+      s = run_partition(c, *p, ib->d_indices, ib->num_indices);
+      if (s != GP_OK) return s;
+    }
+    a.starts = p->d_starts;
+    a.num_batches_dev = p->d_count;
+    a.max_batch_idx = 3 * cfg.max_tris;
+    a.ucap = cfg.max_unique;
+  } else {
+    const uint32_t S = default_batch(cfg);
+    a.static_batch_tris = S / 3;
+    a.num_batches = (T + a.static_batch_tris - 1) / a.static_batch_tris;
+    a.max_batch_idx = S;
+    a.ucap = S;
+  }
+  if (cfg.hash_slots && cfg.hash_slots < a.ucap)
+    return fail(c, GP_ERR_INVALID, "hash_slots must be at least the unique-vertex capacity of a batch");
+  a.hash_slots = cfg.hash_slots ? cfg.hash_slots : next_pow2(2 * a.ucap);
+  a.hash_slots = std::max(a.hash_slots, next_pow2(threads));
+  a.hash_bits = log2u(a.hash_slots);
+  a.sort_n = next_pow2(a.max_batch_idx);
+  const size_t smem = batched_smem_bytes(dedup, (int)shader, a, (int)threads);
+  if (smem > 227 * 1024)
+    return fail(c, GP_ERR_UNSUPPORTED, "batch configuration needs more than 227 KB of shared memory");
+  const uint64_t key = (2ull << 56) | ((uint64_t)dedup << 48) | ((uint64_t)dyn << 47) | ((uint64_t)shader << 40) |
+                       ((uint64_t)threads << 24) | (uint64_t)smem;
+  int bpsm;
+  auto it = c->occ.find(key);
+  if (it != c->occ.end()) {
+    bpsm = it->second;
+  } else {
+    bpsm = batched_blocks_per_sm(dedup, dyn, (int)shader, (int)threads, smem);
+    c->occ[key] = bpsm;
+  }
+  if (bpsm <= 0) return fail(c, GP_ERR_UNSUPPORTED, "draw kernel cannot be resident with this configuration");
+  uint64_t grid = (uint64_t)c->sms * bpsm;
+  if (!dyn) grid = std::min<uint64_t>(grid, a.num_batches);
+  if (std::getenv("GP_VERBOSE") && c->logged.insert(key).second)
+    std::fprintf(stderr, "[gp] batched dedup=%d dyn=%d shader=%u threads=%u smem=%zu blocks/SM=%d grid=%llu slots=%u\n",
+                 dedup, (int)dyn, shader, threads, smem, bpsm, (unsigned long long)grid, a.hash_slots);
+  t.device_counts = true;
+  GP_CUDA(c, launch_batched(dedup, dyn, a, u, (int)shader, (int)threads, (int)std::max<uint64_t>(grid, 1), smem,
+                            c->stream));
+  return GP_OK;
+}
+
+gp_status submit_locked(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* vb, uint32_t shader,
+                        const void* uniforms, uint32_t ubytes, const gp_out_buf* ob, uint64_t* out_ticket) {
+  gp_status s = check_index_buf(c, ib);
+  if (s != GP_OK) return s;
+  if (!vb || !ob) return fail(c, GP_ERR_INVALID, "vertex_buf or out_tris is NULL");
+  if (shader > GP_SHADER_LOAD) return fail(c, GP_ERR_INVALID, "unknown shader_id");
+  if (vb->num_vertices >= 0x80000000ull) return fail(c, GP_ERR_INVALID, "num_vertices must be < 2^31");
+  const uint32_t need_stride = shader == GP_SHADER_SKIN ? 64 : 32;
+  const uint32_t need_fmt = shader == GP_SHADER_SKIN ? GP_VFMT_SKIN64 : vb->format;
+  if (vb->format != GP_VFMT_PNU32 && vb->format != GP_VFMT_SKIN64)
+    return fail(c, GP_ERR_INVALID, "unknown vertex format");
+  if (vb->format != need_fmt) return fail(c, GP_ERR_INVALID, "the skinning shader needs GP_VFMT_SKIN64 vertices");
+  if (vb->stride_bytes < need_stride || vb->stride_bytes % 16)
+    return fail(c, GP_ERR_INVALID, "stride_bytes too small for the format or not a multiple of 16");
+  if (vb->num_vertices && (!vb->d_vertices || reinterpret_cast<uintptr_t>(vb->d_vertices) % 16))
+    return fail(c, GP_ERR_INVALID, "d_vertices NULL or not 16-byte aligned");
+  const uint64_t T = ib->num_indices / 3;
+  const uint64_t need = T * 3 * out_floats((int)shader) * 4;
+  if (T && (!ob->d_out || reinterpret_cast<uintptr_t>(ob->d_out) % 16))
+    return fail(c, GP_ERR_INVALID, "d_out NULL or not 16-byte aligned");
+  if (ob->capacity_bytes < need) return fail(c, GP_ERR_INVALID, "out_tris capacity_bytes too small");
+  Uniforms u;
+  s = make_uniforms(c, shader, uniforms, ubytes, u);
+  if (s != GP_OK) return s;
+
+  // a free device record: fold the oldest draw if the ring is full
+  if (c->inflight.size() >= kRing) {
+    s = sync_locked(c, c->inflight.front().id, 0);
+    if (s != GP_OK && s != GP_ERR_INDEX_RANGE) return s;
+  }
+  Ticket t;
+  t.id = c->next_ticket++;
+  t.slot = (uint32_t)(t.id % kRing);
+  t.ev0 = get_event(c);
+  t.ev1 = get_event(c);
+  if (!t.ev0 || !t.ev1) return fail(c, GP_ERR_CUDA, "cudaEventCreate failed");
+  DevRec* rec = c->d_rec + t.slot;
+  GP_CUDA(c, cudaEventRecord(t.ev0, c->stream));
+  GP_CUDA(c, cudaMemsetAsync(rec, 0, sizeof(DevRec), c->stream));
+  s = enqueue_draw(c, ib, vb, shader, u, ob, t, rec);
+  if (s != GP_OK) {
+    put_event(c, t.ev0);
+    put_event(c, t.ev1);
+    return s;
+  }
+  GP_CUDA(c, cudaEventRecord(t.ev1, c->stream));
+  c->inflight.push_back(t);
+  if (out_ticket) *out_ticket = t.id;
+  return GP_OK;
+}
+
+gp_status ensure_buf(gp_ctx* c, void** p, size_t* cap, size_t need) {
+  if (*cap >= need && *p) return GP_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *cap = 0;
+  GP_CUDA(c, cudaMalloc(p, std::max<size_t>(need, 256)));
+  *cap = std::max<size_t>(need, 256);
+  return GP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gp_status gp_create(const gp_config* cfg_in, gp_ctx** out) {
+  if (!out) return fail(nullptr, GP_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!cfg_in) return fail(nullptr, GP_ERR_INVALID, "cfg is NULL");
+  gp_config cfg = *cfg_in;
+  if (cfg.variant < GP_NAIVE || cfg.variant > GP_PHASH)
+    return fail(nullptr, cfg.variant == GP_AUTO ? GP_ERR_UNSUPPORTED : GP_ERR_INVALID,
+                "variant must be GP_NAIVE..GP_PHASH for a single-draw context");
+  if (cfg.mode != GP_BATCH_STATIC && cfg.mode != GP_BATCH_DYNAMIC) return fail(nullptr, GP_ERR_INVALID, "bad mode");
+  if (!cfg.max_unique) cfg.max_unique = 256;
+  if (!cfg.max_tris) cfg.max_tris = 341;
+  if (!cfg.probe_k) cfg.probe_k = 4;
+  if (!cfg.segment_tris) cfg.segment_tris = 4096;
+  if (!cfg.threads_per_group) cfg.threads_per_group = cfg.variant == GP_WARP ? 64 : 256;
+  cfg.batch_indices = default_batch(cfg);
+  const uint32_t th = cfg.threads_per_group;
+  if (th % 32 || th == 0) return fail(nullptr, GP_ERR_INVALID, "threads_per_group must be a multiple of 32");
+  if (cfg.variant == GP_NAIVE || cfg.variant == GP_WARP) {
+    if (th > 256) return fail(nullptr, GP_ERR_INVALID, "naive/warp blocks are at most 256 threads");
+  } else if ((th & (th - 1)) || th > 512) {
+    return fail(nullptr, GP_ERR_INVALID, "sort/hash/phash threads_per_group must be a power of two <= 512");
+  }
+  if (cfg.batch_indices % 3) return fail(nullptr, GP_ERR_INVALID, "batch_indices must be a multiple of 3");
+  if (cfg.mode == GP_BATCH_DYNAMIC && (cfg.variant == GP_NAIVE || cfg.variant == GP_WARP))
+    return fail(nullptr, GP_ERR_INVALID, "naive and warp voting use static batches");
+  if (cfg.variant == GP_WARP && cfg.batch_indices > 384)
+    return fail(nullptr, GP_ERR_INVALID, "warp voting batches are at most 384 indices");
+  if (cfg.variant >= GP_SORT && cfg.mode == GP_BATCH_STATIC && cfg.batch_indices > 4095)
+    return fail(nullptr, GP_ERR_INVALID, "static batches are at most 4095 indices");
+  if (cfg.max_unique < 3 || cfg.max_unique > 4096) return fail(nullptr, GP_ERR_INVALID, "max_unique must be in 3..4096");
+  if (cfg.max_tris < 1 || cfg.max_tris > 1365) return fail(nullptr, GP_ERR_INVALID, "max_tris must be in 1..1365");
+  if (cfg.hash_slots && (cfg.hash_slots & (cfg.hash_slots - 1)))
+    return fail(nullptr, GP_ERR_INVALID, "hash_slots must be a power of two");
+  if (cfg.variant == GP_NAIVE && cfg.batch_indices != 3 * th)
+    return fail(nullptr, GP_ERR_INVALID, "naive batch_indices is 3 x threads_per_group");
+
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0)
+    return fail(nullptr, GP_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  if (cfg.device < 0 || cfg.device >= ndev) return fail(nullptr, GP_ERR_INVALID, "bad device ordinal");
+  e = cudaSetDevice(cfg.device);
+  if (e != cudaSuccess) return fail(nullptr, GP_ERR_CUDA, cudaGetErrorString(e));
+  gp_ctx* c = new gp_ctx();
+  c->cfg = cfg;
+  c->device = cfg.device;
+  c->stream = static_cast<cudaStream_t>(cfg.stream);
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, cfg.device);
+  if ((e = cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaMalloc(&c->d_rec, sizeof(DevRec) * (kRing + 1))) != cudaSuccess ||
+      (e = cudaMallocHost(&c->h_rec, sizeof(DevRec) * (kRing + 1))) != cudaSuccess ||
+      (e = cudaMemset(c->d_rec, 0, sizeof(DevRec) * (kRing + 1))) != cudaSuccess) {
+    gp_status s = fail(nullptr, e == cudaErrorMemoryAllocation ? GP_ERR_OOM : GP_ERR_CUDA, cudaGetErrorString(e));
+    gp_destroy(c);
+    return s;
+  }
+  *out = c;
+  return GP_OK;
+}
+
+gp_status gp_destroy(gp_ctx* c) {
+  if (!c) return GP_ERR_INVALID;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    for (Ticket& t : c->inflight) {
+      put_event(c, t.ev0);
+      put_event(c, t.ev1);
+    }
+    c->inflight.clear();
+    for (auto& kv : c->parts) release_partition(kv.second);
+    release_partition(c->temp_part);
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    if (c->d_rec) cudaFree(c->d_rec);
+    if (c->h_rec) cudaFreeHost(c->h_rec);
+    if (c->h_idx) cudaFree(c->h_idx);
+    if (c->h_vtx) cudaFree(c->h_vtx);
+    if (c->h_out) cudaFree(c->h_out);
+    if (c->aux) cudaStreamDestroy(c->aux);
+  }
+  delete c;
+  return GP_OK;
+}
+
+gp_status gp_partition(gp_ctx* c, const gp_index_buf* ib, uint64_t* out_handle, uint64_t* out_num_batches) {
+  if (!c) return GP_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  if (!out_handle) return fail(c, GP_ERR_INVALID, "out_handle is NULL");
+  gp_status s = check_index_buf(c, ib);
+  if (s != GP_OK) return s;
+  Partition p;
+  s = size_partition(c, p, ib->num_indices, false);
+  if (s != GP_OK) {
+    release_partition(p);
+    return s;
+  }
+  p.idx = ib->d_indices;
+  s = run_partition(c, p, ib->d_indices, ib->num_indices);
+  if (s != GP_OK) {
+    release_partition(p);
+    return s;
+  }
+  if (cudaEventCreateWithFlags(&p.done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(p.done, c->stream) != cudaSuccess) {
+    release_partition(p);
+    return fail(c, GP_ERR_CUDA, "event for the partition");
+  }
+  const uint64_t h = c->next_part++;
+  c->parts[h] = p;
+  *out_handle = h;
+  if (out_num_batches) {
+    Partition& q = c->parts[h];
+    GP_CUDA(c, cudaEventSynchronize(q.done));
+    uint32_t cnt = 0;
+    GP_CUDA(c, cudaMemcpy(&cnt, q.d_count, 4, cudaMemcpyDeviceToHost));
+    q.count = cnt;
+    q.count_known = true;
+    *out_num_batches = cnt;
+  }
+  return GP_OK;
+}
+
+gp_status gp_partition_starts(gp_ctx* c, uint64_t handle, uint32_t* d_starts, uint64_t capacity,
+                              uint64_t* out_num_batches) {
+  if (!c) return GP_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  auto it = c->parts.find(handle);
+  if (it == c->parts.end()) return fail(c, GP_ERR_INVALID, "unknown partition handle");
+  Partition& p = it->second;
+  GP_CUDA(c, cudaEventSynchronize(p.done));
+  uint32_t cnt = 0;
+  GP_CUDA(c, cudaMemcpy(&cnt, p.d_count, 4, cudaMemcpyDeviceToHost));
+  p.count = cnt;
+  p.count_known = true;
+  if (out_num_batches) *out_num_batches = cnt;
+  if (d_starts) {
+    if (capacity < (uint64_t)cnt + 1) return fail(c, GP_ERR_INVALID, "capacity < batches + 1");
+    GP_CUDA(c, cudaMemcpy(d_starts, p.d_starts, ((size_t)cnt + 1) * 4, cudaMemcpyDeviceToDevice));
+  }
+  return GP_OK;
+}
+
+gp_status gp_partition_release(gp_ctx* c, uint64_t handle) {
+  if (!c) return GP_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  auto it = c->parts.find(handle);
+  if (it == c->parts.end()) return fail(c, GP_ERR_INVALID, "unknown partition handle");
+  cudaEventSynchronize(it->second.done);
+  cudaStreamSynchronize(c->stream);  // draws that read the starts are done
+  release_partition(it->second);
+  c->parts.erase(it);
+  return GP_OK;
+}
+
+gp_status gp_submit_drawcall(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* vb, uint32_t shader_id,
+                             const void* uniforms, uint32_t uniforms_bytes, const gp_out_buf* out_tris,
+                             uint64_t* out_ticket) {
+  if (!c) return GP_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  return submit_locked(c, ib, vb, shader_id, uniforms, uniforms_bytes, out_tris, out_ticket);
+}
+
+gp_status gp_sync(gp_ctx* c, uint64_t ticket, uint32_t timeout_ms) {
+  if (!c) return GP_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  return sync_locked(c, ticket, timeout_ms);
+}
+
+gp_status gp_stats(gp_ctx* c, gp_stats_t* out, int reset) {
+  if (!c || !out) return GP_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  gp_status s = sync_locked(c, 0, 0);
+  std::memset(out, 0, sizeof(*out));
+  out->draws = c->s_draws;
+  out->triangles = c->s_tris;
+  out->indices = c->s_idx;
+  out->invocations = c->s_inv;
+  out->batches = c->s_batches;
+  out->busy_ms = c->s_busy;
+  out->bytes_moved = c->s_bytes;
+  out->last_error = (uint32_t)c->last_status;
+  if (!c->s_lat.empty()) {
+    std::vector<float> v = c->s_lat;
+    std::sort(v.begin(), v.end());
+    auto pct = [&](double q) {
+      const size_t i = (size_t)std::min<double>(v.size() - 1, std::ceil(q * v.size()) - 1);
+      return (double)v[i];
+    };
+    out->p50_ms = pct(0.50);
+    out->p99_ms = pct(0.99);
+  }
+  if (reset) {
+    c->s_draws = c->s_tris = c->s_idx = c->s_inv = c->s_batches = c->s_bytes = 0;
+    c->s_busy = 0.0;
+    c->s_lat.clear();
+    c->last_status = GP_OK;
+    c->last_error.clear();
+  }
+  return s == GP_ERR_INDEX_RANGE ? GP_OK : s;
+}
+
+gp_status gp_draw_host(gp_ctx* c, const uint32_t* indices_host, uint64_t num_indices, const void* vertices_host,
+                       uint64_t num_vertices, uint32_t stride_bytes, uint32_t format, uint32_t shader_id,
+                       const void* uniforms, uint32_t uniforms_bytes, float* out_host, uint64_t out_capacity_bytes) {
+  if (!c) return GP_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  if ((num_indices && !indices_host) || (num_vertices && !vertices_host) || (num_indices && !out_host))
+    return fail(c, GP_ERR_INVALID, "NULL host buffer");
+  if (shader_id > GP_SHADER_LOAD) return fail(c, GP_ERR_INVALID, "unknown shader_id");
+  const uint64_t T = num_indices / 3;
+  const size_t out_bytes = (size_t)T * 3 * out_floats((int)shader_id) * 4;
+  if (out_capacity_bytes < out_bytes) return fail(c, GP_ERR_INVALID, "out capacity too small");
+  gp_status s;
+  if ((s = ensure_buf(c, &c->h_idx, &c->h_idx_cap, num_indices * 4)) != GP_OK) return s;
+  if ((s = ensure_buf(c, &c->h_vtx, &c->h_vtx_cap, num_vertices * stride_bytes)) != GP_OK) return s;
+  if ((s = ensure_buf(c, &c->h_out, &c->h_out_cap, out_bytes)) != GP_OK) return s;
+  if (num_indices) GP_CUDA(c, cudaMemcpyAsync(c->h_idx, indices_host, num_indices * 4, cudaMemcpyHostToDevice, c->stream));
+  if (num_vertices)
+    GP_CUDA(c, cudaMemcpyAsync(c->h_vtx, vertices_host, num_vertices * stride_bytes, cudaMemcpyHostToDevice, c->stream));
+  gp_index_buf ib{static_cast<const uint32_t*>(c->h_idx), num_indices, 0};
+  gp_vertex_buf vb{c->h_vtx, num_vertices, stride_bytes, format};
+  gp_out_buf ob{static_cast<float*>(c->h_out), out_bytes, nullptr, nullptr, 0};
+  uint64_t ticket = 0;
+  s = submit_locked(c, &ib, &vb, shader_id, uniforms, uniforms_bytes, &ob, &ticket);
+  if (s != GP_OK) return s;
+  if (out_bytes) GP_CUDA(c, cudaMemcpyAsync(out_host, c->h_out, out_bytes, cudaMemcpyDeviceToHost, c->stream));
+  GP_CUDA(c, cudaStreamSynchronize(c->stream));
+  return sync_locked(c, ticket, 0);
+}
+
+uint32_t gp_out_floats(uint32_t shader_id) { return shader_id <= GP_SHADER_LOAD ? (uint32_t)out_floats((int)shader_id) : 0u; }
+
+uint64_t gp_static_batch_count(gp_ctx* c, uint64_t num_indices) {
+  if (!c || c->cfg.mode != GP_BATCH_STATIC) return 0;
+  const uint64_t S = c->cfg.batch_indices;
+  return (num_indices + S - 1) / S;
+}
+
+const char* gp_last_error(gp_ctx* c) {
+  if (!c) return g_create_error.c_str();
+  return c->last_error.c_str();
+}
+
+const char* gp_status_string(gp_status s) { return status_name(s); }
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+// Internal interface between the C-ABI runtime (gp_api.cpp) and the kernel
+// launchers (*.cu).  Plain structs, passed by value to the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gp {
+
+// Device error word bits (OR-ed by kernels, read by gp_sync).
+enum : uint32_t {
+  EBIT_INDEX_RANGE = 1u,  // an index >= num_vertices
+  EBIT_TIMEOUT = 2u,      // a bounded mbarrier wait gave up
+  EBIT_CAPACITY = 4u,     // a batch exceeded a table/buffer capacity (internal)
+};
+
+// Counter slots in the context's device counter array (uint64).
+enum : int {
+  CNT_INVOCATIONS = 0,
+  CNT_BATCHES = 1,
+  CNT_UNIQUE = 2,
+  CNT_SLOTS = 8,
+};
+
+constexpr uint32_t kInvalidId = 0xFFFFFFFEu;  // canonical out-of-range id
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;      // empty hash slot / padding key
+constexpr int kMaxEnvelopeDirs = 16;
+constexpr int kEnvelopeTerms = 32;
+
+// Shader uniforms as the kernels see them (kernel parameter, by value).
+struct Uniforms {
+  float mvp[16];
+  float nrm[9];
+  uint32_t steps;        // LOAD
+  float d;               // ENVELOPE
+  uint32_t num_dirs;     // ENVELOPE
+  float inv_dirs;        // ENVELOPE: 1 / num_dirs
+  float dirs[kMaxEnvelopeDirs * 3];
+  float coef[kEnvelopeTerms];  // ENVELOPE: 1/k!, k = 0..31
+  float palette[64 * 12];      // SKIN
+};
+
+// One draw as the kernels see it.
+struct DrawArgs {
+  const uint32_t* idx;           // index buffer
+  uint32_t num_idx;              // 3T
+  uint32_t num_tris;             // T
+  const unsigned char* verts;    // vertex buffer
+  uint32_t num_verts;
+  uint32_t stride;               // bytes
+  float* out;                    // T * 3 * K floats
+  uint32_t* corner_ids;          // optional
+  uint32_t* batch_inv;           // optional
+  uint32_t batch_cap;            // entries in batch_inv
+  // batching
+  uint32_t static_batch_tris;    // static: triangles per batch (S / 3)
+  uint32_t num_batches;          // static: batch count
+  const uint32_t* starts;        // dynamic: batch starts (triangles), count+1 entries
+  const uint32_t* num_batches_dev;  // dynamic: device batch count
+  uint32_t max_batch_idx;        // capacity: indices per batch
+  uint32_t ucap;                 // capacity: unique vertices per batch
+  uint32_t hash_slots;           // power of two
+  uint32_t hash_bits;            // log2(hash_slots)
+  uint32_t sort_n;               // power of two >= max_batch_idx
+  uint32_t probe_k;
+  // bookkeeping
+  unsigned long long* counters;  // CNT_* slots
+  uint32_t* err;                 // error word
+};
+
+struct PartitionArgs {
+  const uint32_t* idx;
+  uint32_t num_tris;
+  uint32_t max_unique;
+  uint32_t max_tris;
+  uint32_t segment_tris;     // > 0
+  uint32_t num_segments;
+  uint32_t seg_cap;          // batch-start slots per segment
+  uint32_t table_slots;      // per-warp hash slots (power of two)
+  uint32_t table_bits;
+  uint32_t* seg_starts;      // [num_segments * seg_cap]
+  uint32_t* seg_counts;      // [num_segments]
+  uint32_t* starts;          // out: [total + 1]
+  uint32_t* num_batches;     // out: total (device)
+  uint32_t* err;
+};
+
+enum Dedup : int { DEDUP_SORT = 0, DEDUP_HASH = 1, DEDUP_PHASH = 2 };
+
+// Launchers (return the launch error).  'shader' is a gp_shader_id.
+cudaError_t launch_naive(const DrawArgs& a, const Uniforms& u, int shader, int block, cudaStream_t s);
+cudaError_t launch_warp(const DrawArgs& a, const Uniforms& u, int shader, int warps_per_block,
+                        int grid, cudaStream_t s);
+int warp_kernel_blocks_per_sm(int shader, int warps_per_block);
+size_t warp_kernel_smem(int shader, int warps_per_block, uint32_t batch_idx);
+
+size_t batched_smem_bytes(int dedup, int shader, const DrawArgs& a, int threads);
+cudaError_t launch_batched(int dedup, bool dynamic, const DrawArgs& a, const Uniforms& u, int shader,
+                           int threads, int grid, size_t smem, cudaStream_t s);
+int batched_blocks_per_sm(int dedup, bool dynamic, int shader, int threads, size_t smem);
+
+size_t partition_smem_bytes(const PartitionArgs& p, int warps);
+cudaError_t launch_partition(const PartitionArgs& p, int warps_per_block, cudaStream_t s);
+
+int out_floats(int shader);  // K
+
+}  // namespace gp
