@@ -378,6 +378,7 @@ gp_status enqueue_draw(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* v
   a.verts = static_cast<const unsigned char*>(vb->d_vertices);
   a.num_verts = (uint32_t)vb->num_vertices;
   a.stride = vb->stride_bytes;
+  a.vec8 = (reinterpret_cast<uintptr_t>(vb->d_vertices) % 32 == 0 && vb->stride_bytes % 32 == 0) ? 1u : 0u;
   a.out = ob->d_out;
   a.corner_ids = ob->d_corner_ids;
   a.batch_inv = ob->d_batch_invocations;
@@ -452,11 +453,16 @@ gp_status enqueue_draw(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* v
   a.hash_slots = std::max(a.hash_slots, next_pow2(threads));
   a.hash_bits = log2u(a.hash_slots);
   a.sort_n = next_pow2(a.max_batch_idx);
+  a.out_chunk = (a.max_batch_idx + 2) / 3;  // the whole batch in one bulk store
+  if (const char* oc = std::getenv("GP_OUT_CHUNK")) {  // tuning override
+    const long v = std::strtol(oc, nullptr, 10);
+    if (v > 0) a.out_chunk = std::min<uint32_t>((uint32_t)v, a.out_chunk);
+  }
   const size_t smem = batched_smem_bytes(dedup, (int)shader, a, (int)threads);
   if (smem > 227 * 1024)
     return fail(c, GP_ERR_UNSUPPORTED, "batch configuration needs more than 227 KB of shared memory");
   const uint64_t key = (2ull << 56) | ((uint64_t)dedup << 48) | ((uint64_t)dyn << 47) | ((uint64_t)shader << 40) |
-                       ((uint64_t)threads << 24) | (uint64_t)smem;
+                       ((uint64_t)threads << 24) | (uint64_t)smem;  // smem < 2^24
   int bpsm;
   auto it = c->occ.find(key);
   if (it != c->occ.end()) {
@@ -469,8 +475,10 @@ gp_status enqueue_draw(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* v
   uint64_t grid = (uint64_t)c->sms * bpsm;
   if (!dyn) grid = std::min<uint64_t>(grid, a.num_batches);
   if (std::getenv("GP_VERBOSE") && c->logged.insert(key).second)
-    std::fprintf(stderr, "[gp] batched dedup=%d dyn=%d shader=%u threads=%u smem=%zu blocks/SM=%d grid=%llu slots=%u\n",
-                 dedup, (int)dyn, shader, threads, smem, bpsm, (unsigned long long)grid, a.hash_slots);
+    std::fprintf(stderr,
+                 "[gp] batched dedup=%d dyn=%d shader=%u threads=%u smem=%zu blocks/SM=%d grid=%llu slots=%u "
+                 "chunk=%u\n",
+                 dedup, (int)dyn, shader, threads, smem, bpsm, (unsigned long long)grid, a.hash_slots, a.out_chunk);
   t.device_counts = true;
   GP_CUDA(c, launch_batched(dedup, dyn, a, u, (int)shader, (int)threads, (int)std::max<uint64_t>(grid, 1), smem,
                             c->stream));

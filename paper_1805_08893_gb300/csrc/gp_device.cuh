@@ -33,19 +33,38 @@ struct VertexIn {
   float w0, w1, w2, w3;
 };
 
+// 32 bytes from a 32-byte-aligned global address in one 256-bit load
+// (read-only path).
+__device__ __forceinline__ void ldg_v8(const void* p, float* r) {
+  asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7])
+               : "l"(p));
+}
+
+// Reads the attributes the shader needs.  vec8: the row is 32-byte aligned,
+// so one 256-bit load per 32 bytes; otherwise 16-byte loads.
 template <int SH>
 __device__ __forceinline__ void fetch_vertex(const unsigned char* verts, uint32_t stride, uint32_t id,
-                                             VertexIn& v) {
-  const float4* p = reinterpret_cast<const float4*>(verts + (size_t)id * stride);
-  float4 a = __ldg(p);
-  float4 b = __ldg(p + 1);
-  v.px = a.x; v.py = a.y; v.pz = a.z;
-  v.nx = a.w; v.ny = b.x; v.nz = b.y;
+                                             VertexIn& v, bool vec8 = false) {
+  const unsigned char* row = verts + (size_t)id * stride;
+  float r[16];
+  if (vec8) {
+    ldg_v8(row, r);
+    if (ShaderTraits<SH>::kSkin) ldg_v8(row + 32, r + 8);
+  } else {
+    const float4* p = reinterpret_cast<const float4*>(row);
+    float4 a = __ldg(p), b = __ldg(p + 1);
+    r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w; r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
+    if (ShaderTraits<SH>::kSkin) {
+      float4 c = __ldg(p + 2), d = __ldg(p + 3);
+      r[8] = c.x; r[9] = c.y; r[10] = c.z; r[11] = c.w; r[12] = d.x; r[13] = d.y; r[14] = d.z; r[15] = d.w;
+    }
+  }
+  v.px = r[0]; v.py = r[1]; v.pz = r[2];
+  v.nx = r[3]; v.ny = r[4]; v.nz = r[5];
   if (ShaderTraits<SH>::kSkin) {
-    float4 c = __ldg(p + 2);
-    float4 d = __ldg(p + 3);
-    v.bones = __float_as_uint(c.x);
-    v.w0 = c.y; v.w1 = c.z; v.w2 = c.w; v.w3 = d.x;
+    v.bones = __float_as_uint(r[8]);
+    v.w0 = r[9]; v.w1 = r[10]; v.w2 = r[11]; v.w3 = r[12];
   } else {
     v.bones = 0; v.w0 = v.w1 = v.w2 = v.w3 = 0.f;
   }
@@ -117,7 +136,7 @@ __device__ __forceinline__ void fetch_and_shade(const DrawArgs& a, const Uniform
                                                 uint32_t id, float* o) {
   if (id < a.num_verts) {
     VertexIn v;
-    fetch_vertex<SH>(a.verts, a.stride, id, v);
+    fetch_vertex<SH>(a.verts, a.stride, id, v, a.vec8 != 0);
     shade_vertex<SH>(u, palette, v, o);
   } else {
 #pragma unroll

@@ -48,6 +48,7 @@ struct DrawArgs {
   const unsigned char* verts;    // vertex buffer
   uint32_t num_verts;
   uint32_t stride;               // bytes
+  uint32_t vec8;                 // 1: vertex rows are 32-byte aligned (256-bit loads)
   float* out;                    // T * 3 * K floats
   uint32_t* corner_ids;          // optional
   uint32_t* batch_inv;           // optional
@@ -63,6 +64,7 @@ struct DrawArgs {
   uint32_t hash_bits;            // log2(hash_slots)
   uint32_t sort_n;               // power of two >= max_batch_idx
   uint32_t probe_k;
+  uint32_t out_chunk;            // triangles per output bulk store (staging buffer size)
   // bookkeeping
   unsigned long long* counters;  // CNT_* slots
   uint32_t* err;                 // error word
