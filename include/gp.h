@@ -223,6 +223,33 @@ gp_status gp_draw_host(gp_ctx* ctx, const uint32_t* indices_host, uint64_t num_i
                        uint32_t format, uint32_t shader_id, const void* uniforms, uint32_t uniforms_bytes,
                        float* out_host, uint64_t out_capacity_bytes);
 
+/* Dynamic partition without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that must not allocate
+ * device memory -- a real-time frame loop, where cudaMalloc can synchronise
+ * the device and stall a frame, or an application that owns all device
+ * memory through its own pool.  It computes the same batch starts as
+ * gp_partition (same rule, same segmentation; segment_tris 0 means 4096) and
+ * needs no context.  Its scratch is one fixed 4 MiB array in the library's
+ * device memory, held on every GPU that loads the library until the process
+ * exits; inputs whose scratch would not fit (about 80 million triangles at
+ * the default limits) return GP_ERR_INVALID -- use gp_partition for those.
+ *   d_indices      device, num_indices indices, 16-byte aligned (read only)
+ *   d_starts       device, receives count + 1 batch starts in triangles; the
+ *                  capacity must be at least num_indices / 3 + 1 entries
+ *   d_num_batches  device, receives the batch count
+ *   stream         cudaStream_t for the work (NULL = legacy default stream)
+ * The work is asynchronous on the stream.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls on a
+ * device share the array and it keeps the last call's contents: calls whose
+ * work overlaps on the GPU race on it, calls ordered on one stream do not.
+ * Returns GP_ERR_INVALID for bad arguments or sizes, GP_ERR_CUDA for a failed
+ * CUDA call, GP_OK otherwise; gp_last_error(NULL) then gives the reason on
+ * the calling thread.  It calls no cudaMalloc or cudaFree. */
+gp_status gp_partition_noalloc(const uint32_t* d_indices, uint64_t num_indices, uint32_t max_unique,
+                               uint32_t max_tris, uint32_t segment_tris, uint32_t* d_starts,
+                               uint64_t starts_capacity, uint32_t* d_num_batches, void* stream);
+
 /* Floats per output corner for a shader (7 or 8), 0 for an unknown id. */
 uint32_t gp_out_floats(uint32_t shader_id);
 

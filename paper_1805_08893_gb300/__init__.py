@@ -19,7 +19,7 @@ from . import _build
 __all__ = [
     "GpError", "gp_create", "gp_destroy", "gp_partition", "gp_partition_starts", "gp_partition_release",
     "gp_submit_drawcall", "gp_sync", "gp_stats", "gp_draw_host", "gp_out_floats", "gp_static_batch_count",
-    "gp_last_error", "gp_status_string", "uniforms_mvp", "uniforms_skin", "uniforms_envelope", "uniforms_load",
+    "gp_last_error", "gp_status_string", "gp_partition_noalloc", "uniforms_mvp", "uniforms_skin", "uniforms_envelope", "uniforms_load",
     "Context", "lib", "library_path",
 ]
 
@@ -113,6 +113,7 @@ def _load():
         "gp_static_batch_count": ([P, U64], U64),
         "gp_last_error": ([P], ctypes.c_char_p),
         "gp_status_string": ([I], ctypes.c_char_p),
+        "gp_partition_noalloc": ([P, U64, U32, U32, U32, P, U64, P, P], I),
     }
     for name, (argt, rest) in sig.items():
         f = getattr(L, name)
@@ -249,6 +250,16 @@ def gp_draw_host(ctx, indices, vertices, shader_id, uniforms, out, fmt=None):
                          ctypes.cast(ctypes.byref(uniforms), ctypes.c_void_p), ctypes.sizeof(uniforms),
                          addr(out), nbytes(out))
     _check(s, ctx)
+
+
+def gp_partition_noalloc(indices, max_unique, max_tris, segment_tris, starts, num_batches, stream=None):
+    """gp_partition_noalloc: batch starts into ``starts`` (int32 CUDA tensor,
+    at least T + 1 entries) and the count into ``num_batches`` (1 entry), with
+    no device allocation.  Asynchronous on ``stream``."""
+    s = lib.gp_partition_noalloc(ctypes.c_void_p(indices.data_ptr()), indices.numel(), max_unique, max_tris,
+                                 segment_tris, ctypes.c_void_p(starts.data_ptr()), starts.numel(),
+                                 ctypes.c_void_p(num_batches.data_ptr()), _stream_handle(stream))
+    _check(s)
 
 
 def gp_out_floats(shader_id: int) -> int:

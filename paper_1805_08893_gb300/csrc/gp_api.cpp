@@ -87,6 +87,8 @@ thread_local std::string g_create_error;
 
 }  // namespace
 
+void gp::set_thread_error(const char* msg) { g_create_error = msg; }
+
 struct gp_ctx {
   std::mutex mu;
   gp_config cfg{};

@@ -106,4 +106,7 @@ cudaError_t launch_partition(const PartitionArgs& p, int warps_per_block, cudaSt
 
 int out_floats(int shader);  // K
 
+// Sets the calling thread's context-free error text (gp_last_error(NULL)).
+void set_thread_error(const char* msg);
+
 }  // namespace gp

@@ -16,6 +16,8 @@
 //     the batch there.
 // A second kernel turns the per-segment lists into one array of batch
 // starts (exclusive scan of the segment counts, then a copy).
+#include <algorithm>
+
 #include "gp_device.cuh"
 
 namespace gp {
@@ -158,6 +160,11 @@ cudaError_t launch_partition(const PartitionArgs& p, int warps_per_block, cudaSt
     partition_gather_kernel<<<1, 32, 0, s>>>(p, p.seg_counts);
     return cudaGetLastError();
   }
+  // as many warps per block as fit in shared memory (large unique limits
+  // need large per-warp tables)
+  const size_t per_warp = partition_smem_bytes(p, 1);
+  warps_per_block = (int)std::min<size_t>((size_t)warps_per_block, (227u * 1024u) / per_warp);
+  if (warps_per_block < 1) return cudaErrorInvalidValue;
   const size_t smem = partition_smem_bytes(p, warps_per_block);
   cudaError_t e = cudaFuncSetAttribute(partition_segments_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
