@@ -223,6 +223,173 @@ gp_status gp_draw_host(gp_ctx* ctx, const uint32_t* indices_host, uint64_t num_i
                        uint32_t format, uint32_t shader_id, const void* uniforms, uint32_t uniforms_bytes,
                        float* out_host, uint64_t out_capacity_bytes);
 
+/* ---------------------------------------------------------------------------
+ * Frames: many draw calls in one persistent launch.
+ *
+ * The draws of a frame are fused into one persistent kernel launch, replayed
+ * from a captured CUDA graph.  Each draw keeps its own method, batch size and
+ * threads per group; GP_AUTO takes them from the context's autotune table
+ * (gp_autotune).  The batches of every draw are handled exactly as in a
+ * single draw of that configuration (Sections 3.3-3.4), so each draw's
+ * output is the same as its single-draw output.
+ * ------------------------------------------------------------------------- */
+
+/* One draw of a frame.  Buffers follow the single-draw rules (gp_index_buf's
+ * partition field is ignored: the frame partitions its dynamic draws when it
+ * is created). */
+typedef struct gp_draw_desc {
+  gp_index_buf index_buf;
+  gp_vertex_buf vertex_buf;
+  gp_out_buf out;
+  uint32_t shader_id;
+  uint32_t uniforms_bytes;
+  const void* uniforms;
+  int32_t variant;            /* GP_NAIVE..GP_PHASH, or GP_AUTO (autotune table) */
+  int32_t mode;               /* gp_batch_mode for sort/hash/phash */
+  uint32_t batch_indices;     /* static S [warp 96, sort/hash/phash 255] */
+  uint32_t max_unique;        /* dynamic N [256] */
+  uint32_t max_tris;          /* dynamic triangle cap [floor((4N - 1) / 3)] */
+  uint32_t threads_per_group; /* sort/hash/phash: 64, 128 or 256 [256] */
+} gp_draw_desc;
+
+/* The configuration a frame draw runs with (after GP_AUTO is resolved). */
+typedef struct gp_draw_config {
+  int32_t variant;
+  int32_t mode;
+  uint32_t batch_indices;
+  uint32_t max_unique;
+  uint32_t max_tris;
+  uint32_t threads_per_group;
+  uint64_t batches;           /* batches of the draw in this frame */
+} gp_draw_config;
+
+/* One row of the autotune table: draws with this shader and a triangle count
+ * in [tris_lo, tris_hi) run with 'config' (its 'batches' field unused). */
+typedef struct gp_autotune_entry {
+  uint32_t shader_id;
+  uint32_t tris_lo, tris_hi;
+  uint32_t pad;
+  gp_draw_config config;
+  double us_per_draw;         /* measured time of the winning configuration */
+} gp_autotune_entry;
+
+typedef struct gp_frame gp_frame;
+
+/* Builds a frame: validates every draw, resolves GP_AUTO, partitions the
+ * dynamic draws (load-time preprocessing, Section 3.4), uploads the draw
+ * table and captures the launch in a CUDA graph.  The buffers and uniforms
+ * are referenced (buffers) or copied (uniforms) as in gp_submit_drawcall; the
+ * buffers must stay valid for the frame's lifetime.  Waits for the
+ * partitions.  GP_ERR_INVALID / GP_ERR_UNSUPPORTED name the first bad draw in
+ * gp_last_error. */
+gp_status gp_frame_create(gp_ctx* ctx, const gp_draw_desc* draws, uint32_t num_draws, gp_frame** out);
+
+/* Launches the frame on the context's stream (a graph launch).  The ticket
+ * works with gp_sync and gp_stats like a draw's; its statistics count every
+ * draw of the frame.  A frame's previous launch is waited for first. */
+gp_status gp_frame_submit(gp_frame* frame, uint64_t* out_ticket);
+
+/* Replaces one draw's uniforms (copied, ordered before the next launch). */
+gp_status gp_frame_set_uniforms(gp_frame* frame, uint32_t draw, const void* uniforms, uint32_t uniforms_bytes);
+
+/* The configuration draw 'draw' runs with. */
+gp_status gp_frame_draw_config(gp_frame* frame, uint32_t draw, gp_draw_config* out);
+
+/* Waits for the frame's last launch and frees it. */
+gp_status gp_frame_destroy(gp_frame* frame);
+
+/* Autotuner: groups the sample draws by shader and power-of-two triangle
+ * count, times candidate configurations (method; static batch size or
+ * dynamic unique limit; threads per group) on up to four samples of each
+ * group with the frame kernel, 'reps' launches each, and stores the fastest
+ * per group in the context's table (replacing rows of the same group).
+ * Draws referenced here are read and their outputs overwritten. */
+gp_status gp_autotune(gp_ctx* ctx, const gp_draw_desc* samples, uint32_t num_samples, uint32_t reps);
+
+/* Copies the autotune table (count rows; up to capacity are written). */
+gp_status gp_autotune_table(gp_ctx* ctx, gp_autotune_entry* out, uint32_t capacity, uint32_t* count);
+
+/* Replaces the autotune table (e.g. one saved from an earlier run). */
+gp_status gp_autotune_set_table(gp_ctx* ctx, const gp_autotune_entry* entries, uint32_t count);
+
+/* ---------------------------------------------------------------------------
+ * Serving: a persistent request loop with continuous batching.
+ *
+ * Meshes are registered once (host copies); a mesh is made resident on the
+ * device when a request needs it, within a memory budget, and the least
+ * recently used meshes without active requests are evicted to make room.
+ * Requests (mesh, shader, uniforms, output) queue up; a native server thread
+ * admits them as memory and slots free up, and every step launches one
+ * persistent kernel over batches taken from all active requests, so requests
+ * that arrive while others are on the GPU join the next step.  Batches stay
+ * request-local: each request's output is the same as its single draw.  Up
+ * to 'streams' steps are in flight on the device at once.  Latency is
+ * measured from submission to the completion of the request's last batch.
+ * ------------------------------------------------------------------------- */
+
+typedef struct gp_server gp_server;
+
+typedef struct gp_serve_config {
+  uint64_t mem_budget_bytes;  /* device bytes for resident meshes [20 GiB] */
+  uint32_t streams;           /* steps in flight at once [2] */
+  uint32_t step_max_batches;  /* batches per step [2048] */
+  uint32_t max_active;        /* requests admitted at once [4096] */
+  int32_t variant;            /* method for every request: GP_NAIVE..GP_PHASH or GP_AUTO [GP_HASH] */
+  int32_t mode;               /* gp_batch_mode (sort/hash/phash) [GP_BATCH_DYNAMIC] */
+  uint32_t batch_indices;     /* as in gp_draw_desc */
+  uint32_t max_unique;
+  uint32_t max_tris;
+  uint32_t threads_per_group;
+} gp_serve_config;
+
+typedef struct gp_serve_stats {
+  uint64_t submitted, completed;
+  uint64_t triangles, invocations, steps;
+  uint64_t uploads, evictions, resident_bytes;
+  double p50_ms, p99_ms, max_ms; /* request latency */
+  double busy_ms;                /* summed device time of the steps */
+  double wall_ms;                /* first submission to last completion */
+  uint32_t last_error;           /* gp_status of the last failed step, or GP_OK */
+  uint32_t pad;
+} gp_serve_stats;
+
+/* Starts a server (and its thread) on the context's device.  The context
+ * must outlive the server. */
+gp_status gp_server_create(gp_ctx* ctx, const gp_serve_config* cfg, gp_server** out);
+
+/* Registers a mesh: the host buffers are copied; the mesh is uploaded on
+ * first use.  Returns its id in *out_mesh. */
+gp_status gp_server_add_mesh(gp_server* server, const uint32_t* indices_host, uint64_t num_indices,
+                             const void* vertices_host, uint64_t num_vertices, uint32_t stride_bytes,
+                             uint32_t format, uint64_t* out_mesh);
+
+/* Queues a request: draw 'mesh' with the shader into d_out (device, caller-
+ * owned, valid until the request completes).  Uniforms are copied.
+ * GP_ERR_BUSY if the mesh alone exceeds the memory budget. */
+gp_status gp_server_submit(gp_server* server, uint64_t mesh, uint32_t shader_id, const void* uniforms,
+                           uint32_t uniforms_bytes, float* d_out, uint64_t out_capacity_bytes,
+                           uint64_t* out_request);
+
+/* Submits n requests at their arrival times (seconds after the call starts)
+ * from the calling thread; returns after the last submission.  The request
+ * ids go to out_requests (may be NULL). */
+gp_status gp_server_replay(gp_server* server, uint32_t n, const double* arrival_s, const uint64_t* meshes,
+                           const uint32_t* shader_ids, const void* const* uniforms, const uint32_t* uniforms_bytes,
+                           float* const* d_outs, const uint64_t* out_capacity_bytes, uint64_t* out_requests);
+
+/* Waits until request 'request' (0 = every request submitted so far) has
+ * completed, up to timeout_ms (0 = no limit).  Returns the request's status. */
+gp_status gp_server_wait(gp_server* server, uint64_t request, uint32_t timeout_ms);
+
+/* Latency of a completed request, in ms. */
+gp_status gp_server_latency(gp_server* server, uint64_t request, double* out_ms);
+
+/* Statistics of completed requests; reset != 0 clears them afterwards. */
+gp_status gp_server_stats(gp_server* server, gp_serve_stats* out, int reset);
+
+/* Waits for all requests, stops the thread and frees device memory. */
+gp_status gp_server_destroy(gp_server* server);
+
 /* Dynamic partition without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that must not allocate
  * device memory -- a real-time frame loop, where cudaMalloc can synchronise

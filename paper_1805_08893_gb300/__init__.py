@@ -19,7 +19,9 @@ from . import _build
 __all__ = [
     "GpError", "gp_create", "gp_destroy", "gp_partition", "gp_partition_starts", "gp_partition_release",
     "gp_submit_drawcall", "gp_sync", "gp_stats", "gp_draw_host", "gp_out_floats", "gp_static_batch_count",
-    "gp_last_error", "gp_status_string", "gp_partition_noalloc", "uniforms_mvp", "uniforms_skin", "uniforms_envelope", "uniforms_load",
+    "gp_last_error", "gp_status_string", "gp_partition_noalloc", "gp_frame_create", "gp_frame_submit",
+    "gp_frame_set_uniforms", "gp_frame_draw_config", "gp_frame_destroy", "gp_autotune", "gp_autotune_table",
+    "gp_autotune_set_table", "draw_desc", "uniforms_mvp", "uniforms_skin", "uniforms_envelope", "uniforms_load",
     "Context", "lib", "library_path",
 ]
 
@@ -82,6 +84,25 @@ class gp_stats_t(ctypes.Structure):
                 ("last_error", ctypes.c_uint32)]
 
 
+class gp_draw_desc(ctypes.Structure):
+    _fields_ = [("index_buf", gp_index_buf), ("vertex_buf", gp_vertex_buf), ("out", gp_out_buf),
+                ("shader_id", ctypes.c_uint32), ("uniforms_bytes", ctypes.c_uint32), ("uniforms", ctypes.c_void_p),
+                ("variant", ctypes.c_int32), ("mode", ctypes.c_int32), ("batch_indices", ctypes.c_uint32),
+                ("max_unique", ctypes.c_uint32), ("max_tris", ctypes.c_uint32),
+                ("threads_per_group", ctypes.c_uint32)]
+
+
+class gp_draw_config(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("mode", ctypes.c_int32), ("batch_indices", ctypes.c_uint32),
+                ("max_unique", ctypes.c_uint32), ("max_tris", ctypes.c_uint32),
+                ("threads_per_group", ctypes.c_uint32), ("batches", ctypes.c_uint64)]
+
+
+class gp_autotune_entry(ctypes.Structure):
+    _fields_ = [("shader_id", ctypes.c_uint32), ("tris_lo", ctypes.c_uint32), ("tris_hi", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32), ("config", gp_draw_config), ("us_per_draw", ctypes.c_double)]
+
+
 class GpError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(message)
@@ -114,6 +135,14 @@ def _load():
         "gp_last_error": ([P], ctypes.c_char_p),
         "gp_status_string": ([I], ctypes.c_char_p),
         "gp_partition_noalloc": ([P, U64, U32, U32, U32, P, U64, P, P], I),
+        "gp_frame_create": ([P, ctypes.POINTER(gp_draw_desc), U32, ctypes.POINTER(P)], I),
+        "gp_frame_submit": ([P, ctypes.POINTER(U64)], I),
+        "gp_frame_set_uniforms": ([P, U32, P, U32], I),
+        "gp_frame_draw_config": ([P, U32, ctypes.POINTER(gp_draw_config)], I),
+        "gp_frame_destroy": ([P], I),
+        "gp_autotune": ([P, ctypes.POINTER(gp_draw_desc), U32, U32], I),
+        "gp_autotune_table": ([P, ctypes.POINTER(gp_autotune_entry), U32, ctypes.POINTER(U32)], I),
+        "gp_autotune_set_table": ([P, ctypes.POINTER(gp_autotune_entry), U32], I),
     }
     for name, (argt, rest) in sig.items():
         f = getattr(L, name)
@@ -260,6 +289,101 @@ def gp_partition_noalloc(indices, max_unique, max_tris, segment_tris, starts, nu
                                  segment_tris, ctypes.c_void_p(starts.data_ptr()), starts.numel(),
                                  ctypes.c_void_p(num_batches.data_ptr()), _stream_handle(stream))
     _check(s)
+
+
+# ---------------------------------------------------------------------------
+# frames and the autotuner
+# ---------------------------------------------------------------------------
+
+def draw_desc(indices, vertices, shader_id, uniforms, out, corner_ids=None, batch_invocations=None,
+              variant=GP_AUTO, mode=GP_BATCH_STATIC, batch_indices=0, max_unique=0, max_tris=0,
+              threads_per_group=0, num_vertices=None, fmt=None):
+    """A gp_draw_desc for gp_frame_create / gp_autotune (keeps ``uniforms``
+    referenced until the call that copies it)."""
+    d = gp_draw_desc()
+    d.index_buf = _index_buf(indices)
+    d.vertex_buf = _vertex_buf(vertices, num_vertices, fmt)
+    d.out = gp_out_buf(out.data_ptr(), out.numel() * out.element_size(),
+                       None if corner_ids is None else corner_ids.data_ptr(),
+                       None if batch_invocations is None else batch_invocations.data_ptr(),
+                       0 if batch_invocations is None else batch_invocations.numel())
+    d.shader_id = shader_id
+    d.uniforms_bytes = ctypes.sizeof(uniforms)
+    d.uniforms = ctypes.cast(ctypes.byref(uniforms), ctypes.c_void_p)
+    d.variant = VARIANTS.get(variant, variant) if isinstance(variant, str) else variant
+    d.mode = mode
+    d.batch_indices = batch_indices
+    d.max_unique = max_unique
+    d.max_tris = max_tris
+    d.threads_per_group = threads_per_group
+    d._keep = uniforms  # the blob must outlive the C call
+    return d
+
+
+def _desc_array(descs):
+    arr = (gp_draw_desc * max(1, len(descs)))()
+    for i, d in enumerate(descs):
+        arr[i] = d
+    return arr
+
+
+def gp_frame_create(ctx, descs):
+    """gp_frame_create: ``descs`` is a list of draw_desc(...) entries."""
+    arr = _desc_array(descs)
+    h = ctypes.c_void_p()
+    _check(lib.gp_frame_create(ctx, arr, len(descs), ctypes.byref(h)), ctx)
+    return h
+
+
+def gp_frame_submit(frame, ctx=None):
+    t = ctypes.c_uint64()
+    _check(lib.gp_frame_submit(frame, ctypes.byref(t)), ctx)
+    return t.value
+
+
+def gp_frame_set_uniforms(frame, draw, uniforms, ctx=None):
+    _check(lib.gp_frame_set_uniforms(frame, draw, ctypes.cast(ctypes.byref(uniforms), ctypes.c_void_p),
+                                     ctypes.sizeof(uniforms)), ctx)
+
+
+def _config_dict(k):
+    return {name: getattr(k, name) for name, _ in gp_draw_config._fields_}
+
+
+def gp_frame_draw_config(frame, draw) -> dict:
+    k = gp_draw_config()
+    _check(lib.gp_frame_draw_config(frame, draw, ctypes.byref(k)))
+    return _config_dict(k)
+
+
+def gp_frame_destroy(frame):
+    _check(lib.gp_frame_destroy(frame))
+
+
+def gp_autotune(ctx, descs, reps=3):
+    arr = _desc_array(descs)
+    _check(lib.gp_autotune(ctx, arr, len(descs), reps), ctx)
+
+
+def gp_autotune_table(ctx) -> list:
+    n = ctypes.c_uint32()
+    _check(lib.gp_autotune_table(ctx, None, 0, ctypes.byref(n)), ctx)
+    arr = (gp_autotune_entry * max(1, n.value))()
+    _check(lib.gp_autotune_table(ctx, arr, n.value, ctypes.byref(n)), ctx)
+    return [{"shader_id": e.shader_id, "tris_lo": e.tris_lo, "tris_hi": e.tris_hi, "config": _config_dict(e.config),
+             "us_per_draw": e.us_per_draw} for e in arr[: n.value]]
+
+
+def gp_autotune_set_table(ctx, rows):
+    arr = (gp_autotune_entry * max(1, len(rows)))()
+    for i, r in enumerate(rows):
+        arr[i].shader_id = r["shader_id"]
+        arr[i].tris_lo = r["tris_lo"]
+        arr[i].tris_hi = r["tris_hi"]
+        for name, _ in gp_draw_config._fields_:
+            setattr(arr[i].config, name, r["config"][name])
+        arr[i].us_per_draw = r.get("us_per_draw", 0.0)
+    _check(lib.gp_autotune_set_table(ctx, arr, len(rows)), ctx)
 
 
 def gp_out_floats(shader_id: int) -> int:

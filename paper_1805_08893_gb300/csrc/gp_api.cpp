@@ -17,52 +17,23 @@
 #include <unordered_set>
 #include <vector>
 
-#include "gp.h"
-#include "gp_internal.h"
+#include "gp_context.h"
 
 using namespace gp;
 
 namespace {
+thread_local std::string g_create_error;
+}  // namespace
 
-constexpr uint32_t kRing = 1024;   // in-flight draws with their own device record
-
-struct alignas(128) DevRec {
-  uint32_t err;
-  uint32_t pad;
-  unsigned long long cnt[15];
-};
-static_assert(sizeof(DevRec) == 128, "device record layout");
-
-struct Ticket {
-  uint64_t id = 0;
-  uint32_t slot = 0;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  uint64_t tris = 0, indices = 0;
-  uint64_t host_inv = 0, host_batches = 0;  // counts known on the host (naive)
-  bool device_counts = false;
-  uint64_t out_bytes = 0;
-  uint32_t stride = 0;
-};
-
-struct Partition {
-  const uint32_t* idx = nullptr;
-  uint64_t num_idx = 0;
-  uint32_t* d_starts = nullptr;  // count + 1 entries
-  uint32_t* d_count = nullptr;
-  uint32_t* d_seg = nullptr;     // seg_starts, then seg_counts (2 x nseg)
-  uint32_t max_batches = 0;
-  uint32_t num_segments = 0, seg_cap = 0;
-  uint32_t max_unique = 0, max_tris = 0, segment_tris = 0;
-  cudaEvent_t done = nullptr;
-  bool count_known = false;
-  uint64_t count = 0;
-};
+namespace gp {
+namespace rt {
 
 uint32_t next_pow2(uint32_t x) {
   uint32_t p = 1;
   while (p < x) p <<= 1;
   return p;
 }
+
 uint32_t log2u(uint32_t x) {
   uint32_t b = 0;
   while ((1u << b) < x) ++b;
@@ -83,47 +54,13 @@ const char* status_name(gp_status s) {
   return "GP_ERR_UNKNOWN";
 }
 
-thread_local std::string g_create_error;
-
-}  // namespace
+}  // namespace rt
+}  // namespace gp
 
 void gp::set_thread_error(const char* msg) { g_create_error = msg; }
 
-struct gp_ctx {
-  std::mutex mu;
-  gp_config cfg{};
-  cudaStream_t stream = nullptr;
-  cudaStream_t aux = nullptr;
-  int device = 0;
-  int sms = 0;
-  DevRec* d_rec = nullptr;
-  DevRec* h_rec = nullptr;  // pinned mirror
-  std::deque<Ticket> inflight;
-  uint64_t next_ticket = 1;
-  std::vector<cudaEvent_t> events;
-  std::unordered_map<uint64_t, Partition> parts;
-  uint64_t next_part = 1;
-  Partition temp_part;  // submit-time partition scratch (dynamic draw without a handle)
-  // statistics of folded draws
-  uint64_t s_draws = 0, s_tris = 0, s_idx = 0, s_inv = 0, s_batches = 0, s_bytes = 0;
-  double s_busy = 0.0;
-  std::vector<float> s_lat;
-  // errors
-  gp_status last_status = GP_OK;
-  std::string last_error;
-  // host-draw staging
-  void* h_idx = nullptr;
-  size_t h_idx_cap = 0;
-  void* h_vtx = nullptr;
-  size_t h_vtx_cap = 0;
-  void* h_out = nullptr;
-  size_t h_out_cap = 0;
-  // occupancy cache: key -> blocks per SM
-  std::unordered_map<uint64_t, int> occ;
-  std::unordered_set<uint64_t> logged;
-};
-
-namespace {
+namespace gp {
+namespace rt {
 
 gp_status fail(gp_ctx* c, gp_status s, const std::string& msg) {
   if (c) {
@@ -140,11 +77,6 @@ gp_status cuda_fail(gp_ctx* c, cudaError_t e, const char* what) {
               std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-#define GP_CUDA(ctx, call)                                   \
-  do {                                                       \
-    cudaError_t e_ = (call);                                 \
-    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
-  } while (0)
 
 cudaEvent_t get_event(gp_ctx* c) {
   if (!c->events.empty()) {
@@ -208,19 +140,25 @@ gp_status fold(gp_ctx* c, uint64_t upto) {
   while (!c->inflight.empty() && c->inflight.front().id <= upto) {
     Ticket t = c->inflight.front();
     c->inflight.pop_front();
-    const DevRec& r = c->h_rec[t.slot];
+    DevRec ext{};
+    if (t.ext_rec) {  // a frame keeps its own record
+      GP_CUDA(c, cudaMemcpyAsync(&c->h_rec[t.slot], t.ext_rec, sizeof(DevRec), cudaMemcpyDeviceToHost, c->aux));
+      GP_CUDA(c, cudaStreamSynchronize(c->aux));
+      ext = c->h_rec[t.slot];
+    }
+    const DevRec& r = t.ext_rec ? ext : c->h_rec[t.slot];
     float ms = 0.f;
     cudaEventElapsedTime(&ms, t.ev0, t.ev1);
     put_event(c, t.ev0);
     put_event(c, t.ev1);
     const uint64_t inv = t.device_counts ? r.cnt[CNT_INVOCATIONS] : t.host_inv;
     const uint64_t bat = t.device_counts ? r.cnt[CNT_BATCHES] : t.host_batches;
-    c->s_draws += 1;
+    c->s_draws += t.draws;
     c->s_tris += t.tris;
     c->s_idx += t.indices;
     c->s_inv += inv;
     c->s_batches += bat;
-    c->s_bytes += 4 * t.indices + (uint64_t)t.stride * inv + t.out_bytes;
+    c->s_bytes += 4 * t.indices + t.vertex_bytes_per_inv * inv + t.out_bytes;
     c->s_busy += ms;
     c->s_lat.push_back(ms);
     gp_status s = GP_OK;
@@ -324,10 +262,11 @@ gp_status run_partition(gp_ctx* c, Partition& p, const uint32_t* idx, uint64_t n
 }
 
 // Sizes (and allocates if needed) a partition for num_idx indices.
-gp_status size_partition(gp_ctx* c, Partition& p, uint64_t num_idx, bool reuse_alloc) {
+gp_status size_partition(gp_ctx* c, Partition& p, uint64_t num_idx, bool reuse_alloc, uint32_t max_unique,
+                         uint32_t max_tris, uint32_t segment_tris) {
   const uint32_t T = (uint32_t)(num_idx / 3);
-  const uint32_t nu = c->cfg.max_unique, mt = c->cfg.max_tris;
-  const uint32_t seg = c->cfg.segment_tris == GP_SEGMENT_NONE ? std::max(T, 1u) : c->cfg.segment_tris;
+  const uint32_t nu = max_unique, mt = max_tris;
+  const uint32_t seg = segment_tris == GP_SEGMENT_NONE ? std::max(T, 1u) : segment_tris;
   const uint32_t min_tris = std::max(1u, std::min(mt, (nu - 2 + 2) / 3));
   const uint32_t nseg = T ? (T + seg - 1) / seg : 0;
   const uint32_t seg_cap = (std::min(seg, std::max(T, 1u)) + min_tris - 1) / min_tris + 1;
@@ -390,7 +329,7 @@ gp_status enqueue_draw(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* v
   a.probe_k = cfg.probe_k;
   t.tris = T;
   t.indices = ib->num_indices;
-  t.stride = vb->stride_bytes;
+  t.vertex_bytes_per_inv = vb->stride_bytes;
   t.out_bytes = (uint64_t)T * 3 * out_floats((int)shader) * 4;
   if (T == 0) return GP_OK;
   const uint32_t threads = cfg.threads_per_group;
@@ -432,7 +371,7 @@ gp_status enqueue_draw(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* v
         return fail(c, GP_ERR_INVALID, "partition handle belongs to another index buffer");
     } else {
       p = &c->temp_part;
-      gp_status s = size_partition(c, *p, ib->num_indices, true);
+      gp_status s = size_partition(c, *p, ib->num_indices, true, cfg.max_unique, cfg.max_tris, cfg.segment_tris);
       if (s != GP_OK) return s;
       p->idx = ib->d_indices;
       s = run_partition(c, *p, ib->d_indices, ib->num_indices);
@@ -487,8 +426,8 @@ gp_status enqueue_draw(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* v
   return GP_OK;
 }
 
-gp_status submit_locked(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* vb, uint32_t shader,
-                        const void* uniforms, uint32_t ubytes, const gp_out_buf* ob, uint64_t* out_ticket) {
+gp_status check_draw(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* vb, uint32_t shader,
+                     const gp_out_buf* ob) {
   gp_status s = check_index_buf(c, ib);
   if (s != GP_OK) return s;
   if (!vb || !ob) return fail(c, GP_ERR_INVALID, "vertex_buf or out_tris is NULL");
@@ -508,21 +447,37 @@ gp_status submit_locked(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* 
   if (T && (!ob->d_out || reinterpret_cast<uintptr_t>(ob->d_out) % 16))
     return fail(c, GP_ERR_INVALID, "d_out NULL or not 16-byte aligned");
   if (ob->capacity_bytes < need) return fail(c, GP_ERR_INVALID, "out_tris capacity_bytes too small");
-  Uniforms u;
-  s = make_uniforms(c, shader, uniforms, ubytes, u);
-  if (s != GP_OK) return s;
+  return GP_OK;
+}
 
+gp_status new_ticket(gp_ctx* c, Ticket& t) {
   // a free device record: fold the oldest draw if the ring is full
   if (c->inflight.size() >= kRing) {
-    s = sync_locked(c, c->inflight.front().id, 0);
+    gp_status s = sync_locked(c, c->inflight.front().id, 0);
     if (s != GP_OK && s != GP_ERR_INDEX_RANGE) return s;
   }
-  Ticket t;
   t.id = c->next_ticket++;
   t.slot = (uint32_t)(t.id % kRing);
   t.ev0 = get_event(c);
   t.ev1 = get_event(c);
-  if (!t.ev0 || !t.ev1) return fail(c, GP_ERR_CUDA, "cudaEventCreate failed");
+  if (!t.ev0 || !t.ev1) {
+    put_event(c, t.ev0);
+    put_event(c, t.ev1);
+    return fail(c, GP_ERR_CUDA, "cudaEventCreate failed");
+  }
+  return GP_OK;
+}
+
+gp_status submit_locked(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* vb, uint32_t shader,
+                        const void* uniforms, uint32_t ubytes, const gp_out_buf* ob, uint64_t* out_ticket) {
+  gp_status s = check_draw(c, ib, vb, shader, ob);
+  if (s != GP_OK) return s;
+  Uniforms u;
+  s = make_uniforms(c, shader, uniforms, ubytes, u);
+  if (s != GP_OK) return s;
+  Ticket t;
+  s = new_ticket(c, t);
+  if (s != GP_OK) return s;
   DevRec* rec = c->d_rec + t.slot;
   GP_CUDA(c, cudaEventRecord(t.ev0, c->stream));
   GP_CUDA(c, cudaMemsetAsync(rec, 0, sizeof(DevRec), c->stream));
@@ -548,7 +503,10 @@ gp_status ensure_buf(gp_ctx* c, void** p, size_t* cap, size_t need) {
   return GP_OK;
 }
 
-}  // namespace
+}  // namespace rt
+}  // namespace gp
+
+using namespace gp::rt;
 
 extern "C" {
 
@@ -645,7 +603,7 @@ gp_status gp_partition(gp_ctx* c, const gp_index_buf* ib, uint64_t* out_handle, 
   gp_status s = check_index_buf(c, ib);
   if (s != GP_OK) return s;
   Partition p;
-  s = size_partition(c, p, ib->num_indices, false);
+  s = size_partition(c, p, ib->num_indices, false, c->cfg.max_unique, c->cfg.max_tris, c->cfg.segment_tris);
   if (s != GP_OK) {
     release_partition(p);
     return s;

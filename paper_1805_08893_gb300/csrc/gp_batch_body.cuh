@@ -1,0 +1,399 @@
+// The per-batch work of the reuse methods, shared by the single-draw kernel
+// (one thread block per batch) and the multi-draw frame kernel (one thread
+// group per batch, several groups per block):
+//   * dedup_and_shade -- find the batch's unique indices (Algorithm 2 sort,
+//     Algorithm 3 hash, Section 3.4 parallel hash) and shade each once;
+//   * fill_stage     -- write a run of assembled triangles, in input order,
+//     into a shared staging buffer.
+// 'tid'/'NT' are the thread's index in and the size of its group; 'sync' is
+// the group barrier (__syncthreads for a whole block, a named barrier for a
+// part of one).
+#pragma once
+
+#include "gp_device.cuh"
+
+namespace gp {
+
+constexpr int kIdsPerRound = 4;  // indices a thread handles before its warp shades the new ones
+constexpr uint16_t kNoRank = 0xFFFFu;
+
+struct BlockSync {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+
+// Named barrier over the nthreads threads of one group (a multiple of 32).
+struct GroupSync {
+  uint32_t id, nthreads;
+  __device__ __forceinline__ void operator()() const {
+    if (nthreads == 32) __syncwarp();
+    else asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+  }
+};
+
+// Shared-memory working set of one batch.
+struct BatchSmem {
+  uint16_t* map;                // corner position -> slot (hash) or rank (sort)
+  unsigned long long* keys;     // sort: (id << 32 | position)
+  uint32_t* table;              // hash: open-addressing table, kEmpty = free
+  uint16_t* dense;              // hash: slot -> rank
+  uint32_t* uniq;               // rank -> vertex id
+  float* vsh;                   // rank -> shaded vertex (KS floats)
+  uint16_t* wq;                 // this warp's queue of new ranks (32 * kIdsPerRound)
+  uint32_t* ucount;             // unique count of the batch
+  uint32_t* wsum;               // per-warp totals for the sort's scan (>= NT/32 words)
+};
+
+__device__ __forceinline__ uint32_t hash_slot(uint32_t id, uint32_t bits) {
+  return bits ? (id * 2654435769u) >> (32 - bits) : 0u;
+}
+
+template <int SH>
+__device__ __forceinline__ void store_shaded(float* vsh, uint32_t k, const float* o) {
+  constexpr int K = ShaderTraits<SH>::K;
+  constexpr int KS = ShaderTraits<SH>::KS;
+  if (K == 8) {
+    float4* dv = reinterpret_cast<float4*>(vsh + k * KS);
+    dv[0] = make_float4(o[0], o[1], o[2], o[3]);
+    dv[1] = make_float4(o[4], o[5], o[6], o[7]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < K; ++c) vsh[k * KS + c] = o[c];
+  }
+}
+
+// Shades the warp's queue of new vertices (their ranks; the id is uniq[rank])
+// in full-warp passes: two vertices per lane per pass, both loads issued
+// before the math.
+template <int SH>
+__device__ __forceinline__ void shade_queue(const DrawArgs& a, const Uniforms& u, const float* palette, float* vsh,
+                                            const uint32_t* uniq, const uint16_t* q, uint32_t qn, uint32_t lane) {
+  constexpr int K = ShaderTraits<SH>::K;
+  for (uint32_t e = lane; e < qn; e += 64) {
+    const bool has1 = e + 32 < qn;
+    const uint32_t r0 = q[e], r1 = has1 ? q[e + 32] : kNoRank;
+    const uint32_t id0 = r0 != kNoRank ? uniq[r0] : kInvalidId;
+    const uint32_t id1 = r1 != kNoRank ? uniq[r1] : kInvalidId;
+    VertexIn v0, v1;
+    const bool ok0 = id0 < a.num_verts, ok1 = id1 < a.num_verts;
+    if (ok0) fetch_vertex<SH>(a.verts, a.stride, id0, v0, a.vec8 != 0);
+    if (ok1) fetch_vertex<SH>(a.verts, a.stride, id1, v1, a.vec8 != 0);
+    float o[K];
+    if (r0 != kNoRank) {
+      if (ok0) {
+        shade_vertex<SH>(u, palette, v0, o);
+      } else {
+#pragma unroll
+        for (int c = 0; c < K; ++c) o[c] = 0.f;
+        atomicOr(a.err, EBIT_INDEX_RANGE);
+      }
+      store_shaded<SH>(vsh, r0, o);
+    }
+    if (r1 != kNoRank) {
+      if (ok1) {
+        shade_vertex<SH>(u, palette, v1, o);
+      } else {
+#pragma unroll
+        for (int c = 0; c < K; ++c) o[c] = 0.f;
+        atomicOr(a.err, EBIT_INDEX_RANGE);
+      }
+      store_shaded<SH>(vsh, r1, o);
+    }
+  }
+}
+
+// One compare-exchange of the bitonic network seen from element i holding x,
+// whose partner (i ^ j) holds y: ascending runs where (i & k) == 0; the lower
+// index of a pair keeps the smaller key in an ascending run.
+__device__ __forceinline__ unsigned long long bitonic_keep(unsigned long long x, unsigned long long y, uint32_t i,
+                                                           uint32_t j, uint32_t k) {
+  const bool asc = (i & k) == 0;
+  const bool lower = (i & j) == 0;
+  const bool take_min = lower == asc;
+  const unsigned long long mn = x < y ? x : y, mx = x < y ? y : x;
+  return take_min ? mn : mx;
+}
+
+// Bitonic sort of keys[0..N), N a power of two.  With N = 4 * NT every
+// thread keeps 4 consecutive keys in registers: stages with j <= 2 stay in
+// the thread, 4 <= j <= 64 exchange within the warp by shuffles (partner lane
+// = lane ^ j/4), and only j >= 128 goes through shared memory.  Otherwise the
+// network runs in shared memory; for j <= 32 the pairs touched by one warp
+// stay inside that warp's 64-key blocks (i = 2t - (t mod j), t = 32q + r), so
+// those stages need only a warp barrier.  Leaves the sorted keys in keys[].
+template <class Sync>
+__device__ __forceinline__ void bitonic_sort(unsigned long long* keys, uint32_t N, uint32_t tid, uint32_t NT,
+                                             Sync sync) {
+  if (N == 4 * NT) {
+    unsigned long long r[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) r[e] = keys[4 * tid + e];
+    for (uint32_t k = 2; k <= N; k <<= 1) {
+      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+        if (j >= 128) {
+          sync();  // every thread has read the previous contents
+#pragma unroll
+          for (int e = 0; e < 4; ++e) keys[4 * tid + e] = r[e];
+          sync();
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const uint32_t i = 4 * tid + e;
+            r[e] = bitonic_keep(r[e], keys[i ^ j], i, j, k);
+          }
+        } else if (j >= 4) {
+          const uint32_t lm = j >> 2;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const unsigned long long y = __shfl_xor_sync(kFull, r[e], lm);
+            r[e] = bitonic_keep(r[e], y, 4 * tid + e, j, k);
+          }
+        } else if (j == 2) {
+          unsigned long long s[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) s[e] = bitonic_keep(r[e], r[e ^ 2], 4 * tid + e, 2, k);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) r[e] = s[e];
+        } else {
+          unsigned long long s[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) s[e] = bitonic_keep(r[e], r[e ^ 1], 4 * tid + e, 1, k);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) r[e] = s[e];
+        }
+      }
+    }
+    sync();
+#pragma unroll
+    for (int e = 0; e < 4; ++e) keys[4 * tid + e] = r[e];
+    sync();
+    return;
+  }
+  for (uint32_t k = 2; k <= N; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t t = tid; t < N / 2; t += NT) {
+        const uint32_t i = 2 * t - (t & (j - 1));
+        const uint32_t l = i + j;
+        const bool up = (i & k) == 0;
+        const unsigned long long x = keys[i], y = keys[l];
+        if ((x > y) == up) {
+          keys[i] = y;
+          keys[l] = x;
+        }
+      }
+      const uint32_t nj = j > 1 ? (j >> 1) : k;  // j of the next stage
+      if (j >= 64 || nj >= 64) sync();
+      else __syncwarp();
+    }
+  }
+  sync();
+}
+
+// Finds the unique indices of ids[0..n) and shades each once into S.vsh.
+// On return (after a group barrier the caller issues) *S.ucount holds the
+// unique count U, S.uniq[0..U) the ids, and S.map (with S.dense for hash)
+// each corner's rank.  The hash table must be empty on entry; it is left
+// filled (the caller clears it after the barrier).  *S.ucount must be 0 on
+// entry for hash/phash.
+template <int DEDUP, int SH, class Sync>
+__device__ __forceinline__ void dedup_and_shade(const DrawArgs& a, const Uniforms& u, const float* palette,
+                                                const BatchSmem& S, const uint32_t* ids, uint32_t n, uint32_t tid,
+                                                uint32_t NT, Sync sync) {
+  const uint32_t lane = lane_id(), warp = tid >> 5;
+  if (DEDUP == DEDUP_SORT) {
+    // --- Algorithm 2: sort (id, position), tail flags, exclusive prefix sum
+    for (uint32_t i = tid; i < a.sort_n; i += NT) {
+      if (i < n) {
+        uint32_t id = ids[i];
+        id = id < a.num_verts ? id : kInvalidId;
+        S.keys[i] = ((unsigned long long)id << 32) | i;
+      } else {
+        S.keys[i] = ~0ull;
+      }
+    }
+    sync();
+    bitonic_sort(S.keys, a.sort_n, tid, NT, sync);
+    // tail flags over each thread's contiguous run, then a group scan with one
+    // barrier: every thread adds up the totals of the warps before its own
+    const uint32_t ipt = (n + NT - 1) / NT;
+    const uint32_t lo = min(tid * ipt, n), hi = min(lo + ipt, n);
+    uint32_t cnt = 0;
+    for (uint32_t i = lo; i < hi; ++i)
+      cnt += (i == n - 1 || (uint32_t)(S.keys[i] >> 32) != (uint32_t)(S.keys[i + 1] >> 32)) ? 1u : 0u;
+    const uint32_t inc = warp_inclusive_scan(cnt);
+    if (lane == 31) S.wsum[warp] = inc;
+    sync();
+    uint32_t r = inc - cnt;
+    for (uint32_t w = 0; w < warp; ++w) r += S.wsum[w];
+    if (tid == NT - 1) *S.ucount = r + cnt;
+    // walk the run in rounds of kIdsPerRound elements (ipt is the same for
+    // every thread, so the warp's ballots line up); tails go to the warp's
+    // shading queue
+    for (uint32_t off = 0; off < ipt; off += kIdsPerRound) {
+      uint32_t qn = 0;
+#pragma unroll
+      for (int q = 0; q < kIdsPerRound; ++q) {
+        const uint32_t i = lo + off + q;
+        bool tail = false;
+        uint32_t id = 0;
+        if (off + q < ipt && i < hi) {
+          id = (uint32_t)(S.keys[i] >> 32);
+          S.map[(uint32_t)(S.keys[i] & 0xFFFFu)] = (uint16_t)r;
+          tail = (i == n - 1) || id != (uint32_t)(S.keys[i + 1] >> 32);
+        }
+        const uint32_t tm = __ballot_sync(kFull, tail);
+        if (tail) {
+          uint16_t rk = (uint16_t)r;
+          if (r < a.ucap) {
+            S.uniq[r] = id;
+          } else {
+            atomicOr(a.err, EBIT_CAPACITY);
+            rk = kNoRank;
+          }
+          S.wq[qn + __popc(tm & lanemask_lt())] = rk;
+          ++r;
+        }
+        qn += __popc(tm);
+      }
+      __syncwarp();
+      shade_queue<SH>(a, u, palette, S.vsh, S.uniq, S.wq, qn, lane);
+      __syncwarp();
+    }
+  } else {
+    // --- Algorithm 3 / Section 3.4: insert; the thread storing a new id
+    // takes its rank, and the warp shades its new ids together
+    const uint32_t mask = a.hash_slots - 1;
+    for (uint32_t rbase = 0; rbase < n; rbase += kIdsPerRound * NT) {
+      uint32_t qn = 0;  // the warp's queue of new ranks
+#pragma unroll
+      for (int q = 0; q < kIdsPerRound; ++q) {
+        const uint32_t i = rbase + q * NT + tid;
+        const bool active = i < n;
+        uint32_t id = active ? ids[i] : 0u;
+        id = id < a.num_verts ? id : kInvalidId;
+        uint32_t h = hash_slot(id, a.hash_bits);
+        bool is_new = false;
+        if (DEDUP == DEDUP_HASH) {
+          if (active) {
+            for (uint32_t probes = 0;; ++probes) {
+              const uint32_t prev = atomicCAS(&S.table[h], kEmpty, id);
+              if (prev == kEmpty) {
+                is_new = true;
+                break;
+              }
+              if (prev == id) break;
+              h = (h + 1) & mask;
+              if (probes > a.hash_slots) {  // table full: cannot happen within capacity
+                atomicOr(a.err, EBIT_CAPACITY);
+                h = 0;
+                break;
+              }
+            }
+          }
+        } else {
+          bool placed = !active;
+          for (uint32_t p = 0; p < a.probe_k && !placed; ++p) {
+            const uint32_t prev = atomicCAS(&S.table[h], kEmpty, id);
+            if (prev == kEmpty) is_new = true;
+            if (prev == kEmpty || prev == id) placed = true;
+            else h = (h + 1) & mask;
+          }
+          uint32_t pending = __ballot_sync(kFull, !placed);
+          while (pending) {
+            const uint32_t leader = __ffs(pending) - 1;
+            const uint32_t lid = __shfl_sync(kFull, id, leader);
+            uint32_t lh = __shfl_sync(kFull, h, leader);
+            uint32_t found = kEmpty;
+            bool fresh = false;
+            for (uint32_t guard = 0; found == kEmpty; ++guard) {
+              if (guard > a.hash_slots / 16 + 64) {  // table full: cannot happen within capacity
+                if (lane == 0) atomicOr(a.err, EBIT_CAPACITY);
+                found = 0;
+                break;
+              }
+              const uint32_t s = (lh + lane) & mask;
+              const uint32_t val = S.table[s];
+              const uint32_t hit = __ballot_sync(kFull, val == lid);
+              if (hit) {
+                found = (lh + __ffs(hit) - 1) & mask;
+                break;
+              }
+              const uint32_t emp = __ballot_sync(kFull, val == kEmpty);
+              if (emp) {
+                const uint32_t fl = __ffs(emp) - 1;
+                const uint32_t cs = (lh + fl) & mask;
+                uint32_t prev = 0;
+                if (lane == fl) prev = atomicCAS(&S.table[cs], kEmpty, lid);
+                prev = __shfl_sync(kFull, prev, fl);
+                if (prev == kEmpty || prev == lid) {
+                  found = cs;
+                  fresh = prev == kEmpty;
+                } else {
+                  lh = cs;  // the slot was just taken: continue probing from it
+                }
+              } else {
+                lh = (lh + 32) & mask;
+              }
+            }
+            if (lane == leader) {
+              h = found;
+              is_new = fresh;
+            }
+            pending &= pending - 1;
+          }
+        }
+        // warp-aggregated dense ranks for the new ids
+        const uint32_t newmask = __ballot_sync(kFull, is_new);
+        uint32_t wbase = 0;
+        if (newmask) {
+          const uint32_t leader = __ffs(newmask) - 1;
+          if (lane == leader) wbase = atomicAdd(S.ucount, __popc(newmask));
+          wbase = __shfl_sync(kFull, wbase, leader);
+        }
+        if (is_new) {
+          const uint32_t pos = __popc(newmask & lanemask_lt());
+          const uint32_t rk = wbase + pos;
+          if (rk < a.ucap) {
+            S.dense[h] = (uint16_t)rk;
+            S.uniq[rk] = id;
+            S.wq[qn + pos] = (uint16_t)rk;
+          } else {
+            atomicOr(a.err, EBIT_CAPACITY);
+            S.wq[qn + pos] = kNoRank;
+          }
+        }
+        qn += __popc(newmask);
+        if (active) S.map[i] = (uint16_t)h;
+      }
+      __syncwarp();
+      shade_queue<SH>(a, u, palette, S.vsh, S.uniq, S.wq, qn, lane);
+      __syncwarp();
+    }
+  }
+}
+
+// Writes corners [cbase, cbase + nc) of the batch (local corner numbering)
+// to st[0..nc*K): the shaded result of each corner's vertex, in input order.
+// Also records each corner's source vertex in a.corner_ids[gcorner0 + ...].
+template <int DEDUP, int SH>
+__device__ __forceinline__ void fill_stage(const DrawArgs& a, const BatchSmem& S, float* st, uint32_t cbase,
+                                           uint32_t nc, uint32_t U, uint64_t gcorner0, uint32_t tid, uint32_t NT,
+                                           bool aligned16) {
+  constexpr int K = ShaderTraits<SH>::K;
+  constexpr int KS = ShaderTraits<SH>::KS;
+  for (uint32_t lc = tid; lc < nc; lc += NT) {
+    const uint32_t m = S.map[cbase + lc];
+    uint32_t s = (DEDUP == DEDUP_SORT) ? m : S.dense[m];
+    s = s < U ? s : 0u;  // only reachable after a flagged capacity error; keeps reads in bounds
+    if (K == 8 && aligned16) {
+      const float4* sv = reinterpret_cast<const float4*>(S.vsh + s * KS);
+      float4* dv = reinterpret_cast<float4*>(st + lc * K);
+      dv[0] = sv[0];
+      dv[1] = sv[1];
+    } else {
+#pragma unroll
+      for (int c = 0; c < K; ++c) st[lc * K + c] = S.vsh[s * KS + c];
+    }
+    if (a.corner_ids != nullptr) a.corner_ids[gcorner0 + lc] = S.uniq[s];
+  }
+}
+
+}  // namespace gp

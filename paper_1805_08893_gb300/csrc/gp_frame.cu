@@ -1,0 +1,276 @@
+// Multi-draw frame: every draw call of a frame in one persistent launch.
+//
+// The draws' batches are cut into work items.  Blocks of 256 threads pull
+// items from a global counter.  An item belongs to one draw and is split
+// among the block's thread groups of that draw's size G (threads per group,
+// chosen per draw; named barriers keep the groups independent):
+//   naive -- one group of 256 threads, one triangle per thread (Section 3.3);
+//   warp  -- eight warps, each runs one static batch by warp voting
+//            (Algorithm 1);
+//   sort / hash / phash -- 256/G groups, each runs one batch (static, or a
+//            dynamic batch from the draw's partition) through the same
+//            dedup-and-shade body as the single-draw kernel.
+// Each group works in its own slice of the block's shared memory, assembles
+// its triangles there and writes them with 16-byte streaming stores.
+#include "gp_batch_body.cuh"
+#include "gp_warp_body.cuh"
+
+namespace gp {
+
+struct FrameSlice {
+  uint32_t off_misc, off_win, off_map, off_keys, off_table, off_dense, off_uniq, off_v, off_stage, off_wq, total;
+};
+
+__host__ __device__ inline uint32_t fr_align(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
+
+// Shared memory of one dedup group (sort/hash/phash).
+__host__ __device__ inline FrameSlice frame_slice(int method, int K, int KS, uint32_t max_idx, uint32_t ucap,
+                                                  uint32_t slots, uint32_t sort_n, uint32_t group) {
+  FrameSlice L;
+  uint32_t o = 0;
+  L.off_misc = o; o += 32 * 4;
+  L.off_win = o; o = fr_align(o + max_idx * 4, 16);
+  L.off_map = o; o = fr_align(o + max_idx * 2, 16);
+  if (method == kFrameSort) {
+    L.off_keys = o; o += sort_n * 8;
+    L.off_table = L.off_dense = 0;
+  } else {
+    L.off_keys = 0;
+    L.off_table = o; o += slots * 4;
+    L.off_dense = o; o = fr_align(o + slots * 2, 16);
+  }
+  L.off_uniq = o; o = fr_align(o + ucap * 4, 16);
+  L.off_v = o; o = fr_align(o + ucap * KS * 4, 16);
+  L.off_stage = o; o = fr_align(o + (fr_align(max_idx, 3) * K + 4) * 4, 16);
+  L.off_wq = o; o = fr_align(o + group * kIdsPerRound * 2, 16);
+  L.total = o;
+  return L;
+}
+
+uint32_t frame_slice_bytes(int method, int shader, uint32_t max_idx, uint32_t ucap, uint32_t slots, uint32_t sort_n,
+                           uint32_t group, uint32_t batch_idx) {
+  const int K = shader == 2 ? 8 : 7;
+  if (method == kFrameNaive) return (kFrameThreads / 32) * 32 * 3 * K * 4;
+  if (method == kFrameWarp) {
+    switch (shader) {
+      case 0: return (kFrameThreads / 32) * WarpSmem<0>::per_warp_bytes(batch_idx);
+      case 1: return (kFrameThreads / 32) * WarpSmem<1>::per_warp_bytes(batch_idx);
+      case 2: return (kFrameThreads / 32) * WarpSmem<2>::per_warp_bytes(batch_idx);
+      default: return (kFrameThreads / 32) * WarpSmem<3>::per_warp_bytes(batch_idx);
+    }
+  }
+  return frame_slice(method, K, K, max_idx, ucap, slots, sort_n, group).total * (kFrameThreads / group);
+}
+
+// 16-byte streaming copy of nfl floats staged at src (16-byte aligned) + pad
+// to dst (= out + g0, with pad = g0 mod 4) by nthreads threads.
+__device__ __forceinline__ void store_staged(float* dst, const float* src, uint32_t pad, uint32_t nfl, uint32_t t,
+                                             uint32_t nthreads) {
+  const float* s = src + pad;
+  const uint32_t head = min(nfl, (4u - pad) & 3u);
+  if (t < head) dst[t] = s[t];
+  const uint32_t n4 = (nfl - head) >> 2;
+  float4* d4 = reinterpret_cast<float4*>(dst + head);
+  const float4* s4 = reinterpret_cast<const float4*>(s + head);
+  for (uint32_t i = t; i < n4; i += nthreads) __stcs(d4 + i, s4[i]);
+  for (uint32_t i = head + (n4 << 2) + t; i < nfl; i += nthreads) dst[i] = s[i];
+}
+
+template <int SH>
+__device__ __forceinline__ void frame_naive(const FrameDraw& D, uint32_t b, unsigned char* slices,
+                                            const float* palette, unsigned long long& inv, unsigned long long& nbat) {
+  constexpr int K = ShaderTraits<SH>::K;
+  constexpr int F = 3 * K;
+  const DrawArgs& a = D.a;
+  const uint32_t tid = threadIdx.x, warp = tid >> 5, lane = lane_id();
+  float* stage = reinterpret_cast<float*>(slices) + warp * (32 * F);
+  const uint32_t tb0 = b * kFrameThreads;
+  const uint32_t ntb = min(kFrameThreads, a.num_tris - tb0);
+  if (tid == 0) {
+    inv += 3ull * ntb;
+    nbat += 1;
+    if (a.batch_inv != nullptr && b < a.batch_cap) a.batch_inv[b] = 3u * ntb;
+  }
+  const uint32_t tw0 = tb0 + warp * 32;
+  if (tw0 >= a.num_tris) return;
+  const uint32_t ntw = min(32u, a.num_tris - tw0);
+  const uint32_t t = tw0 + lane;
+  if (lane < ntw) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const uint32_t id = __ldg(a.idx + 3u * t + k);
+      float o[K];
+      fetch_and_shade<SH>(a, *D.u, palette, id, o);
+#pragma unroll
+      for (int c = 0; c < K; ++c) stage[lane * F + k * K + c] = o[c];
+      if (a.corner_ids != nullptr) a.corner_ids[3u * t + k] = id;
+    }
+  }
+  __syncwarp();
+  store_staged(a.out + (size_t)tw0 * F, stage, 0, ntw * F, lane, 32);
+}
+
+template <int SH>
+__device__ __forceinline__ void frame_warp(const FrameDraw& D, uint32_t item, unsigned char* slices,
+                                           const float* palette, unsigned long long& inv, unsigned long long& nbat) {
+  const DrawArgs& a = D.a;
+  const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
+  const uint32_t j = item * (kFrameThreads / 32) + warp;
+  if (j >= D.num_batches) return;
+  const uint32_t b = D.batch_begin + j;
+  unsigned char* wp = slices + warp * WarpSmem<SH>::per_warp_bytes(3u * a.static_batch_tris);
+  const uint32_t n = warp_vote_batch<SH>(a, *D.u, palette, b, wp, lane);
+  if (lane == 0) {
+    inv += n;
+    nbat += 1;
+    if (a.batch_inv != nullptr && b < a.batch_cap) a.batch_inv[b] = n;
+  }
+}
+
+template <int METHOD, int SH>
+__device__ __forceinline__ void frame_group(const FrameDraw& D, uint32_t item, unsigned char* slices,
+                                            const float* palette, unsigned long long& inv, unsigned long long& nbat) {
+  constexpr int DEDUP = METHOD == kFrameSort ? DEDUP_SORT : (METHOD == kFrameHash ? DEDUP_HASH : DEDUP_PHASH);
+  constexpr int K = ShaderTraits<SH>::K;
+  constexpr int KS = ShaderTraits<SH>::KS;
+  constexpr int F = 3 * K;
+  const DrawArgs& a = D.a;
+  const uint32_t G = D.group;
+  const uint32_t g = threadIdx.x / G, gt = threadIdx.x % G;
+  const uint32_t j = item * (kFrameThreads / G) + g;
+  if (j >= D.num_batches) return;  // the whole group is idle; its barrier is not used
+  const uint32_t b = D.batch_begin + j;
+  const GroupSync sync{g + 1, G};
+  const FrameSlice L = frame_slice(METHOD, K, KS, a.max_batch_idx, a.ucap, a.hash_slots, a.sort_n, G);
+  unsigned char* base = slices + g * L.total;
+  uint32_t* misc = reinterpret_cast<uint32_t*>(base + L.off_misc);
+  uint32_t* win = reinterpret_cast<uint32_t*>(base + L.off_win);
+  float* stage = reinterpret_cast<float*>(base + L.off_stage);
+  BatchSmem S;
+  S.map = reinterpret_cast<uint16_t*>(base + L.off_map);
+  S.keys = reinterpret_cast<unsigned long long*>(base + L.off_keys);
+  S.table = reinterpret_cast<uint32_t*>(base + L.off_table);
+  S.dense = reinterpret_cast<uint16_t*>(base + L.off_dense);
+  S.uniq = reinterpret_cast<uint32_t*>(base + L.off_uniq);
+  S.vsh = reinterpret_cast<float*>(base + L.off_v);
+  S.wq = reinterpret_cast<uint16_t*>(base + L.off_wq) + (gt >> 5) * (32 * kIdsPerRound);
+  S.ucount = misc;
+  S.wsum = misc + 8;
+
+  uint32_t t0, t1;
+  if (D.dynamic) {
+    t0 = __ldg(a.starts + b);
+    t1 = __ldg(a.starts + b + 1);
+  } else {
+    t0 = b * a.static_batch_tris;
+    t1 = min(t0 + a.static_batch_tris, a.num_tris);
+  }
+  const uint32_t n = 3 * (t1 - t0);
+  if (n > a.max_batch_idx) {  // cannot happen with a consistent configuration
+    if (gt == 0) atomicOr(a.err, EBIT_CAPACITY);
+    return;
+  }
+  for (uint32_t i = gt; i < n; i += G) win[i] = __ldg(a.idx + 3 * t0 + i);
+  if (DEDUP != DEDUP_SORT)
+    for (uint32_t s = gt; s < a.hash_slots; s += G) S.table[s] = kEmpty;
+  if (gt == 0) *S.ucount = 0;
+  sync();
+  dedup_and_shade<DEDUP, SH>(a, *D.u, palette, S, win, n, gt, G, sync);
+  sync();
+  const uint32_t U = min(*S.ucount, a.ucap);
+  const size_t g0 = (size_t)t0 * F;
+  const uint32_t pad = (uint32_t)(g0 & 3);
+  fill_stage<DEDUP, SH>(a, S, stage + pad, 0, n, U, 3ull * t0, gt, G, pad == 0);
+  sync();
+  store_staged(a.out + g0, stage, pad, (t1 - t0) * F, gt, G);
+  if (gt == 0) {
+    inv += U;
+    nbat += 1;
+    if (a.batch_inv != nullptr && b < a.batch_cap) a.batch_inv[b] = U;
+  }
+}
+
+template <int SH>
+__device__ __forceinline__ void frame_item(const FrameDraw& D, uint32_t item, unsigned char* slices,
+                                           const float* palette, unsigned long long& inv, unsigned long long& nbat) {
+  switch (D.method) {
+    case kFrameNaive: frame_naive<SH>(D, D.batch_begin + item, slices, palette, inv, nbat); break;
+    case kFrameWarp: frame_warp<SH>(D, item, slices, palette, inv, nbat); break;
+    case kFrameSort: frame_group<kFrameSort, SH>(D, item, slices, palette, inv, nbat); break;
+    case kFrameHash: frame_group<kFrameHash, SH>(D, item, slices, palette, inv, nbat); break;
+    default: frame_group<kFramePHash, SH>(D, item, slices, palette, inv, nbat); break;
+  }
+}
+
+__global__ void __launch_bounds__(kFrameThreads, 3) frame_kernel(const FrameDraw* __restrict__ draws,
+                                                                 uint32_t num_draws, uint32_t total_items,
+                                                                 uint32_t* work, unsigned long long* counters) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* palette = reinterpret_cast<float*>(smem);
+  unsigned char* slices = smem + 768 * 4;
+  __shared__ uint32_t s_item;
+  __shared__ __align__(16) FrameDraw s_draw;  // the current item's draw, read from shared memory
+  unsigned long long inv = 0, nbat = 0;
+  uint32_t pal_draw = 0xFFFFFFFFu, cur_draw = 0xFFFFFFFFu;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(work, 1u);
+    __syncthreads();
+    const uint32_t item = s_item;
+    if (item >= total_items) break;
+    // the draw whose item range holds this item (item_begin is increasing)
+    uint32_t lo = 0, hi = num_draws;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (draws[mid].item_begin <= item) lo = mid;
+      else hi = mid;
+    }
+    if (cur_draw != lo) {  // uniform: every thread found the same draw
+      constexpr uint32_t kWords = sizeof(FrameDraw) / 4;
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(draws + lo);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&s_draw);
+      for (uint32_t i = threadIdx.x; i < kWords; i += blockDim.x) dst[i] = src[i];
+      cur_draw = lo;
+      __syncthreads();
+    }
+    const FrameDraw& D = s_draw;
+    if (D.shader == 1 && pal_draw != lo) {
+      for (uint32_t i = threadIdx.x; i < 768; i += blockDim.x) palette[i] = D.u->palette[i];
+      pal_draw = lo;
+      __syncthreads();
+    }
+    const uint32_t local = item - D.item_begin;
+    switch (D.shader) {
+      case 0: frame_item<0>(D, local, slices, palette, inv, nbat); break;
+      case 1: frame_item<1>(D, local, slices, palette, inv, nbat); break;
+      case 2: frame_item<2>(D, local, slices, palette, inv, nbat); break;
+      default: frame_item<3>(D, local, slices, palette, inv, nbat); break;
+    }
+    __syncthreads();  // the slices are carved anew for the next item
+  }
+  // per-thread partial counts (group leaders, warp leaders) into the record
+  if (inv) atomicAdd(counters + CNT_INVOCATIONS, inv);
+  if (nbat) atomicAdd(counters + CNT_BATCHES, nbat);
+}
+
+size_t frame_smem_bytes() { return 768 * 4 + kFrameSliceBytes; }
+
+int frame_blocks_per_sm() {
+  const size_t smem = frame_smem_bytes();
+  if (cudaFuncSetAttribute(frame_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  cudaFuncSetAttribute(frame_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, frame_kernel, kFrameThreads, smem) != cudaSuccess) return 0;
+  return nb;
+}
+
+cudaError_t launch_frame(const FrameDraw* d_draws, uint32_t num_draws, uint32_t total_items, uint32_t* d_work,
+                         unsigned long long* d_counters, int grid, cudaStream_t s) {
+  const size_t smem = frame_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(frame_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  frame_kernel<<<grid, kFrameThreads, smem, s>>>(d_draws, num_draws, total_items, d_work, d_counters);
+  return cudaGetLastError();
+}
+
+}  // namespace gp

@@ -106,6 +106,31 @@ cudaError_t launch_partition(const PartitionArgs& p, int warps_per_block, cudaSt
 
 int out_floats(int shader);  // K
 
+// ---- multi-draw frame (gp_frame.cu)
+enum FrameMethod : int { kFrameNaive = 0, kFrameWarp = 1, kFrameSort = 2, kFrameHash = 3, kFramePHash = 4 };
+constexpr uint32_t kFrameThreads = 256;          // threads per block of the frame kernel
+constexpr uint32_t kFrameSliceBytes = 64 * 1024;  // shared memory for the groups of one block
+
+struct FrameDraw {
+  DrawArgs a;               // buffers, batching and capacities of the draw (err/counters: the frame's record)
+  const Uniforms* u;        // device copy of the draw's uniforms
+  uint32_t method;          // FrameMethod
+  uint32_t shader;          // gp_shader_id
+  uint32_t dynamic;         // batches from a.starts
+  uint32_t group;           // threads per group G (sort/hash/phash)
+  uint32_t num_batches;     // batches of this entry: [batch_begin, batch_begin + num_batches)
+  uint32_t item_begin;      // first work item of the entry
+  uint32_t items;           // work items of the entry
+  uint32_t batch_begin;     // first batch (a serving step runs a sub-range of a draw)
+};
+
+uint32_t frame_slice_bytes(int method, int shader, uint32_t max_idx, uint32_t ucap, uint32_t slots, uint32_t sort_n,
+                           uint32_t group, uint32_t batch_idx);
+size_t frame_smem_bytes();
+int frame_blocks_per_sm();
+cudaError_t launch_frame(const FrameDraw* d_draws, uint32_t num_draws, uint32_t total_items, uint32_t* d_work,
+                         unsigned long long* d_counters, int grid, cudaStream_t s);
+
 // Sets the calling thread's context-free error text (gp_last_error(NULL)).
 void set_thread_error(const char* msg);
 
