@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--frequency", type=int, default=FREQ, help="geodesic frequency (600 = the benchmark mesh)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--sections", default="heavy,frame,serving",
+                    help="extra workloads after the headline: heavy, frame, serving (comma list, or 'none')")
     ap.add_argument("--clock-warm", type=float, default=1.0,
                     help="seconds of headline draws before its warm-up, so the clock sampler sees the GPU under load")
     return ap.parse_args()
@@ -233,6 +235,253 @@ def reference_arm(args):
 # GPU arm
 # --------------------------------------------------------------------------
 
+def whole_job_rate(local_ms, local_units, dist=None, device="cpu"):
+    """Replicas: every rank times its own steps; the job's step time is the
+    slowest rank's and its rate is all ranks' units over that time.
+    Returns (units per second, max ms per step)."""
+    import torch
+    if dist is None:
+        return local_units / (local_ms * 1e-3), local_ms
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / (float(t.item()) * 1e-3), float(t.item())
+
+
+# --------------------------------------------------------------------------
+# extra workloads (reported beside the headline)
+# --------------------------------------------------------------------------
+
+def fp32_peak_tflops(sms, mhz):
+    """FP32 FMA peak: SMs x 128 lanes x 2 flop x clock."""
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def time_draws(gp, torch, ctx, idx, verts, sid, uni, out, handle, steps, warmup):
+    for _ in range(warmup):
+        gp.gp_submit_drawcall(ctx, idx, verts, sid, uni, out, partition=handle)
+    gp.gp_sync(ctx)
+    gp.gp_stats(ctx, reset=True)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        gp.gp_submit_drawcall(ctx, idx, verts, sid, uni, out, partition=handle)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    st = gp.gp_stats(ctx)
+    return e0.elapsed_time(e1) / steps, st
+
+
+def heavy_section(gp, torch, args):
+    """Heavy per-vertex compute: 1M-vertex / 2M-triangle noisy sphere with the
+    envelope shader (16 directions x 32-term polynomial, inner and outer
+    offsets written); reuse pays where shading dominates."""
+    mesh = mg.geodesic_sphere(316, 4)
+    T, V = mesh.num_tris, mesh.num_vertices
+    sid = gp.GP_SHADER_ENVELOPE
+    uni = gp.uniforms_envelope(mg.envelope_offset(mesh), mg.envelope_directions())
+    idx = torch.from_numpy(mesh.indices.view(np.int32)).cuda()
+    verts = torch.from_numpy(mesh.vertices).cuda()
+    out = torch.empty(T * 24, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    # FMAs per shaded vertex: per direction 3 (dot) + 1 (scale) + 31 (Horner) + 1 (sum), then 6 + 2
+    flops_per_vertex = 2 * (16 * 36 + 8)
+    props = torch.cuda.get_device_properties(0)
+    res = {}
+    for name, variant, mode, extra in [("naive", "naive", 0, {}), ("warp_s96", "warp", 0, {}),
+                                       ("hash_dynamic", "hash", 1, {}), ("phash_dynamic", "phash", 1, {}),
+                                       ("sort_dynamic", "sort", 1, {}), ("hash_static_s768", "hash", 0,
+                                                                         {"batch_indices": 768})]:
+        ctx = gp.gp_create(variant, mode=mode, stream=stream, **extra)
+        handle = 0
+        if mode == 1:
+            handle, _ = gp.gp_partition(ctx, idx)
+        ms, st = time_draws(gp, torch, ctx, idx, verts, sid, uni, out, handle, args.steps, args.warmup)
+        inv = st["invocations"] / max(1, st["draws"])
+        kernel_ms = st["busy_ms"] / max(1, st["draws"])
+        res[name] = {"triangles_per_s": T / (ms * 1e-3), "ms_per_draw": ms, "shading_rate": inv / V,
+                     "gflops_algorithmic": inv * flops_per_vertex / (kernel_ms * 1e-3) / 1e9}
+        if handle:
+            gp.gp_partition_release(ctx, handle)
+        gp.gp_destroy(ctx)
+    naive = res["naive"]["triangles_per_s"]
+    for v in res.values():
+        v["vs_naive"] = v["triangles_per_s"] / naive
+    best = max(res, key=lambda k: res[k]["triangles_per_s"])
+    peak = fp32_peak_tflops(props.multi_processor_count, 2070)
+    return {"workload": f"envelope shader, geodesic sphere f=316 ({V} vertices / {T} triangles)",
+            "flops_per_shaded_vertex": flops_per_vertex, "fp32_peak_tflops_at_2070mhz": peak,
+            "best": best, "best_vs_naive": res[best]["vs_naive"],
+            "naive_fp32_frac": res["naive"]["gflops_algorithmic"] / 1e3 / peak,
+            "variants": res}
+
+
+def frame_section(gp, torch, args):
+    """A frame of 2,000 draw calls (triangle counts log-uniform in [100,
+    50,000], grids and sphere patches, 64-byte skinned vertices, a 64-bone
+    palette each) in one graph-captured persistent launch, configurations
+    chosen per mesh by the autotuner."""
+    t0 = time.time()
+    sizes = mg.frame_sizes()
+    meshes, pals = [], []
+    for k, n in enumerate(sizes):
+        m, pal = mg.skin_mesh(mg.frame_mesh(k, int(n)), k)
+        meshes.append(m)
+        pals.append(pal)
+    gen_s = time.time() - t0
+    stream = torch.cuda.current_stream()
+    ctx = gp.gp_create("hash", stream=stream)
+    bufs, descs = [], []
+    for k, (m, pal) in enumerate(zip(meshes, pals)):
+        M, N = mg.mvp_uniforms(1000 + k)
+        uni = gp.uniforms_skin(M, N, pal)
+        idx = torch.from_numpy(m.indices.view(np.int32)).cuda()
+        verts = torch.from_numpy(m.vertices).cuda()
+        out = torch.empty(m.num_tris * 21, dtype=torch.float32, device="cuda")
+        bufs.append((idx, verts, out, uni))
+        descs.append(gp.draw_desc(idx, verts, gp.GP_SHADER_SKIN, uni, out))
+    T = int(sum(m.num_tris for m in meshes))
+    t1 = time.time()
+    rng = np.random.default_rng(5)
+    sample = [descs[i] for i in rng.choice(len(descs), size=200, replace=False)]
+    gp.gp_autotune(ctx, sample, reps=3)
+    tune_s = time.time() - t1
+    table = gp.gp_autotune_table(ctx)
+
+    def run(frame):
+        for _ in range(args.warmup):
+            gp.gp_frame_submit(frame, ctx)
+        gp.gp_sync(ctx)
+        gp.gp_stats(ctx, reset=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            gp.gp_frame_submit(frame, ctx)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = gp.gp_stats(ctx, reset=True)
+        return e0.elapsed_time(e1) / args.steps, st
+
+    out = {}
+    for name, variant in [("autotuned", gp.GP_AUTO), ("naive", gp.GP_NAIVE), ("hash_dynamic", gp.GP_HASH)]:
+        ds = []
+        for (idx, verts, o, uni) in bufs:
+            ds.append(gp.draw_desc(idx, verts, gp.GP_SHADER_SKIN, uni, o, variant=variant,
+                                   mode=gp.GP_BATCH_DYNAMIC if variant == gp.GP_HASH else gp.GP_BATCH_STATIC))
+        frame = gp.gp_frame_create(ctx, ds)
+        ms, st = run(frame)
+        inv = st["invocations"] / max(1, st["draws"] / len(ds))
+        out[name] = {"ms_per_frame": ms, "triangles_per_s": T / (ms * 1e-3),
+                     "shading_rate": inv / sum(m.num_vertices for m in meshes)}
+        if name == "autotuned":
+            hist = {}
+            for i in range(len(ds)):
+                k = gp.gp_frame_draw_config(frame, i)
+                key = {0: "naive", 1: "warp", 2: "sort", 3: "hash", 4: "phash"}[k["variant"]]
+                key += "_dyn" if k["mode"] == 1 and k["variant"] >= 2 else ""
+                key += f"_G{k['threads_per_group']}"
+                hist[key] = hist.get(key, 0) + 1
+            out[name]["configs"] = hist
+        gp.gp_frame_destroy(frame)
+    # the same draws as separate submissions (no fusion), autotuned methods
+    ms_sep = None
+    try:
+        ctxs = {}
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        cfgs = []
+        for (idx, verts, o, uni), m in zip(bufs, meshes):
+            rows = [r for r in table if r["tris_lo"] <= m.num_tris < r["tris_hi"]]
+            c = rows[0]["config"] if rows else {"variant": 3, "mode": 1}
+            v = {0: "naive", 1: "warp", 2: "sort", 3: "hash", 4: "phash"}[c["variant"]]
+            key = (v, c["mode"], c.get("batch_indices", 0), c.get("max_unique", 0), c.get("max_tris", 0))
+            if key not in ctxs:
+                kw = {}
+                if v in ("sort", "hash", "phash"):
+                    kw = {"batch_indices": c["batch_indices"]} if c["mode"] == 0 else {
+                        "max_unique": c["max_unique"], "max_tris": c["max_tris"]}
+                elif v == "warp":
+                    kw = {"batch_indices": c["batch_indices"]}
+                ctxs[key] = gp.gp_create(v, mode=c["mode"] if v in ("sort", "hash", "phash") else 0,
+                                         stream=stream, **kw)
+            cfgs.append(ctxs[key])
+        for _ in range(2):
+            for c, (idx, verts, o, uni) in zip(cfgs, bufs):
+                gp.gp_submit_drawcall(c, idx, verts, gp.GP_SHADER_SKIN, uni, o)
+        for c in ctxs.values():
+            gp.gp_sync(c)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for c, (idx, verts, o, uni) in zip(cfgs, bufs):
+            gp.gp_submit_drawcall(c, idx, verts, gp.GP_SHADER_SKIN, uni, o)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_sep = e0.elapsed_time(e1)
+        for c in ctxs.values():
+            gp.gp_destroy(c)
+    except Exception as e:  # reported, not fatal
+        ms_sep = f"failed: {e}"
+    gp.gp_destroy(ctx)
+    return {"workload": f"{len(meshes)} skinned draws, {T} triangles, one persistent launch per frame",
+            "gen_s": gen_s, "autotune_s": tune_s, "autotune_rows": len(table), "frames": out,
+            "separate_submissions_ms": ms_sep,
+            "speedup_vs_separate": (ms_sep / out["autotuned"]["ms_per_frame"]) if isinstance(ms_sep, float) else None}
+
+
+def serving_section(gp, torch, args):
+    """Serving: Poisson arrivals, sizes log-uniform in [50, 200,000]
+    triangles from a pool of resident meshes (MVP and skinning shaders),
+    admitted under a 20 GB budget; triangles/s and p50/p99 request latency
+    at several arrival rates."""
+    rng = np.random.default_rng(9)
+    sizes = mg.serving_sizes(5, 192)
+    pool = []
+    for k, n in enumerate(sizes):
+        m = mg.frame_mesh(k, int(n), seed=5)
+        if k % 2:
+            m, pal = mg.skin_mesh(m, k)
+        else:
+            pal = None
+        pool.append((m, pal))
+    ctx = gp.gp_create("hash")
+    srv = gp.gp_server_create(ctx, mem_budget_bytes=20 << 30, streams=3, step_max_batches=2048)
+    mids = [gp.gp_server_add_mesh(srv, m.indices, m.vertices) for m, _ in pool]
+    unis = []
+    for k, (m, pal) in enumerate(pool):
+        M, N = mg.mvp_uniforms(3000 + k)
+        unis.append(gp.uniforms_skin(M, N, pal) if pal is not None else gp.uniforms_mvp(M, N))
+    outs = [torch.empty(m.num_tris * 21, dtype=torch.float32, device="cuda") for m, _ in pool]
+    # warm: every mesh resident once
+    for k in range(len(pool)):
+        gp.gp_server_submit(srv, mids[k], gp.GP_SHADER_SKIN if pool[k][1] is not None else gp.GP_SHADER_MVP,
+                            unis[k], outs[k])
+    gp.gp_server_wait(srv)
+    gp.gp_server_stats(srv, reset=True)
+    res = {}
+    for lam in (5000, 10000, 20000, 50000):
+        dur = 1.0
+        arr = mg.poisson_arrivals(lam, lam, dur)
+        pick = rng.integers(0, len(pool), size=arr.size)
+        ids = gp.gp_server_replay(srv, arr, [mids[i] for i in pick],
+                                  [gp.GP_SHADER_SKIN if pool[i][1] is not None else gp.GP_SHADER_MVP for i in pick],
+                                  [unis[i] for i in pick], [outs[i] for i in pick])
+        gp.gp_server_wait(srv)
+        st = gp.gp_server_stats(srv, reset=True)
+        tris = st["triangles"]
+        res[str(lam)] = {"requests": int(arr.size), "triangles_per_s": tris / (st["wall_ms"] * 1e-3),
+                         "offered_triangles_per_s": float(sum(pool[i][0].num_tris for i in pick) / dur),
+                         "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+                         "device_busy_frac": st["busy_ms"] / max(st["wall_ms"], 1e-9), "steps": st["steps"]}
+        del ids
+    gp.gp_server_destroy(srv)
+    gp.gp_destroy(ctx)
+    return {"workload": f"Poisson requests over {len(pool)} resident meshes (50-200k triangles, MVP/skinning)",
+            "rates": res}
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -332,15 +581,11 @@ def main():
         if sampler:
             sampler.stop()
             clocks = sampler.summary(w0, w1)
-        ms_step = ms_total / args.steps
-        if dist is not None:
-            tt = torch.tensor([ms_step], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ms_step = float(tt.item())
+        rate, ms_step = whole_job_rate(ms_total / args.steps, T, dist, device="cuda")
         inv_per_draw = st["invocations"] / max(1, st["draws"])
         kernel_ms = st["busy_ms"] / max(1, st["draws"])
         results[name] = {
-            "triangles_per_s": world * T / (ms_step * 1e-3),
+            "triangles_per_s": rate,
             "ms_per_draw": ms_step,
             "kernel_ms_mean": kernel_ms,
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
@@ -355,7 +600,7 @@ def main():
             results[name]["triangles_per_s_incl_partition"] = world * T / ((ms_step + part_ms) * 1e-3)
             results[name]["dynamic_batches"] = nbatches
         if name == HEADLINE:
-            head = (ctx, handle, kernel_ms, ms_step, st)
+            head = (ctx, handle, kernel_ms, ms_step, st, rate)
         else:
             if handle:
                 gp.gp_partition_release(ctx, handle)
@@ -363,7 +608,7 @@ def main():
         # keep the next variant's output from reusing stale values
         torch.cuda.synchronize()
 
-    ctx, handle, kernel_ms, ms_step, st = head
+    ctx, handle, kernel_ms, ms_step, st, head_rate = head
     naive_tps = results.get("naive", {}).get("triangles_per_s")
 
     # end to end through the public API from pinned host memory
@@ -406,7 +651,7 @@ def main():
     if rank == 0:
         line = {
             "metric": METRIC,
-            "value": world * T / (ms_step * 1e-3),
+            "value": head_rate,
             "unit": UNIT,
             "n_gpus": world,
             "steps": args.steps,
@@ -435,6 +680,21 @@ def main():
             "variants": results,
             "mesh_gen_s": gen_s,
         }
+        sections = [] if args.sections == "none" else [x for x in args.sections.split(",") if x]
+        if world == 1 and sections:
+            # release the headline mesh before the extra workloads
+            del idx, verts, out
+            torch.cuda.empty_cache()
+            extra = {}
+            for name, fn in (("heavy", heavy_section), ("frame", frame_section), ("serving", serving_section)):
+                if name in sections:
+                    t0 = time.time()
+                    try:
+                        extra[name] = fn(gp, torch, args)
+                    except Exception as e:  # a failing extra workload is reported, not fatal
+                        extra[name] = {"error": repr(e)[:500]}
+                    extra[name]["section_s"] = time.time() - t0
+            line["workloads"] = extra
         print(json.dumps(line))
     if handle:
         gp.gp_partition_release(ctx, handle)

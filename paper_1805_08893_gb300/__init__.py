@@ -21,7 +21,8 @@ __all__ = [
     "gp_submit_drawcall", "gp_sync", "gp_stats", "gp_draw_host", "gp_out_floats", "gp_static_batch_count",
     "gp_last_error", "gp_status_string", "gp_partition_noalloc", "gp_frame_create", "gp_frame_submit",
     "gp_frame_set_uniforms", "gp_frame_draw_config", "gp_frame_destroy", "gp_autotune", "gp_autotune_table",
-    "gp_autotune_set_table", "draw_desc", "uniforms_mvp", "uniforms_skin", "uniforms_envelope", "uniforms_load",
+    "gp_autotune_set_table", "draw_desc", "gp_server_create", "gp_server_add_mesh", "gp_server_submit",
+    "gp_server_replay", "gp_server_wait", "gp_server_latency", "gp_server_stats", "gp_server_destroy", "uniforms_mvp", "uniforms_skin", "uniforms_envelope", "uniforms_load",
     "Context", "lib", "library_path",
 ]
 
@@ -103,6 +104,21 @@ class gp_autotune_entry(ctypes.Structure):
                 ("pad", ctypes.c_uint32), ("config", gp_draw_config), ("us_per_draw", ctypes.c_double)]
 
 
+class gp_serve_config(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("streams", ctypes.c_uint32),
+                ("step_max_batches", ctypes.c_uint32), ("max_active", ctypes.c_uint32), ("variant", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("batch_indices", ctypes.c_uint32), ("max_unique", ctypes.c_uint32),
+                ("max_tris", ctypes.c_uint32), ("threads_per_group", ctypes.c_uint32)]
+
+
+class gp_serve_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("triangles", ctypes.c_uint64),
+                ("invocations", ctypes.c_uint64), ("steps", ctypes.c_uint64), ("uploads", ctypes.c_uint64),
+                ("evictions", ctypes.c_uint64), ("resident_bytes", ctypes.c_uint64), ("p50_ms", ctypes.c_double),
+                ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("busy_ms", ctypes.c_double),
+                ("wall_ms", ctypes.c_double), ("last_error", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+
+
 class GpError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(message)
@@ -143,6 +159,16 @@ def _load():
         "gp_autotune": ([P, ctypes.POINTER(gp_draw_desc), U32, U32], I),
         "gp_autotune_table": ([P, ctypes.POINTER(gp_autotune_entry), U32, ctypes.POINTER(U32)], I),
         "gp_autotune_set_table": ([P, ctypes.POINTER(gp_autotune_entry), U32], I),
+        "gp_server_create": ([P, ctypes.POINTER(gp_serve_config), ctypes.POINTER(P)], I),
+        "gp_server_add_mesh": ([P, P, U64, P, U64, U32, U32, ctypes.POINTER(U64)], I),
+        "gp_server_submit": ([P, U64, U32, P, U32, P, U64, ctypes.POINTER(U64)], I),
+        "gp_server_replay": ([P, U32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(U64), ctypes.POINTER(U32),
+                              ctypes.POINTER(P), ctypes.POINTER(U32), ctypes.POINTER(P), ctypes.POINTER(U64),
+                              ctypes.POINTER(U64)], I),
+        "gp_server_wait": ([P, U64, U32], I),
+        "gp_server_latency": ([P, U64, ctypes.POINTER(ctypes.c_double)], I),
+        "gp_server_stats": ([P, ctypes.POINTER(gp_serve_stats), I], I),
+        "gp_server_destroy": ([P], I),
     }
     for name, (argt, rest) in sig.items():
         f = getattr(L, name)
@@ -384,6 +410,80 @@ def gp_autotune_set_table(ctx, rows):
             setattr(arr[i].config, name, r["config"][name])
         arr[i].us_per_draw = r.get("us_per_draw", 0.0)
     _check(lib.gp_autotune_set_table(ctx, arr, len(rows)), ctx)
+
+
+# ---------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------
+
+def gp_server_create(ctx, mem_budget_bytes=0, streams=0, step_max_batches=0, max_active=0, variant="hash",
+                     mode=GP_BATCH_DYNAMIC, batch_indices=0, max_unique=0, max_tris=0, threads_per_group=0):
+    cfg = gp_serve_config(mem_budget_bytes, streams, step_max_batches, max_active,
+                          VARIANTS.get(variant, variant) if isinstance(variant, str) else variant, mode, batch_indices,
+                          max_unique, max_tris, threads_per_group)
+    h = ctypes.c_void_p()
+    _check(lib.gp_server_create(ctx, ctypes.byref(cfg), ctypes.byref(h)), ctx)
+    return h
+
+
+def gp_server_add_mesh(server, indices, vertices, fmt=None):
+    """Registers a mesh from host arrays (numpy); returns its id."""
+    idx = np.ascontiguousarray(indices, dtype=np.uint32)
+    vtx = np.ascontiguousarray(vertices)
+    stride = vtx.shape[1] * vtx.itemsize
+    if fmt is None:
+        fmt = GP_VFMT_SKIN64 if stride == 64 else GP_VFMT_PNU32
+    m = ctypes.c_uint64()
+    _check(lib.gp_server_add_mesh(server, idx.ctypes.data, idx.size, vtx.ctypes.data, vtx.shape[0], stride, fmt,
+                                  ctypes.byref(m)))
+    return m.value
+
+
+def gp_server_submit(server, mesh, shader_id, uniforms, out):
+    r = ctypes.c_uint64()
+    _check(lib.gp_server_submit(server, mesh, shader_id, ctypes.cast(ctypes.byref(uniforms), ctypes.c_void_p),
+                                ctypes.sizeof(uniforms), ctypes.c_void_p(out.data_ptr()),
+                                out.numel() * out.element_size(), ctypes.byref(r)))
+    return r.value
+
+
+def gp_server_replay(server, arrivals_s, meshes, shader_ids, uniforms, outs):
+    """Submits requests at their arrival times (seconds from the call) from the
+    native side; returns their ids once all are submitted."""
+    n = len(arrivals_s)
+    arr = (ctypes.c_double * n)(*[float(x) for x in arrivals_s])
+    ms = (ctypes.c_uint64 * n)(*[int(x) for x in meshes])
+    sh = (ctypes.c_uint32 * n)(*[int(x) for x in shader_ids])
+    up = (ctypes.c_void_p * n)(*[ctypes.cast(ctypes.byref(u), ctypes.c_void_p).value for u in uniforms])
+    ub = (ctypes.c_uint32 * n)(*[ctypes.sizeof(u) for u in uniforms])
+    op = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    oc = (ctypes.c_uint64 * n)(*[o.numel() * o.element_size() for o in outs])
+    ids = (ctypes.c_uint64 * n)()
+    _check(lib.gp_server_replay(server, n, arr, ms, sh, up, ub, op, oc, ids))
+    return list(ids)
+
+
+def gp_server_wait(server, request=0, timeout_ms=0, raise_on_error=True):
+    s = lib.gp_server_wait(server, request, timeout_ms)
+    if raise_on_error:
+        _check(s)
+    return s
+
+
+def gp_server_latency(server, request) -> float:
+    v = ctypes.c_double()
+    _check(lib.gp_server_latency(server, request, ctypes.byref(v)))
+    return v.value
+
+
+def gp_server_stats(server, reset=False) -> dict:
+    st = gp_serve_stats()
+    _check(lib.gp_server_stats(server, ctypes.byref(st), 1 if reset else 0))
+    return {name: getattr(st, name) for name, _ in gp_serve_stats._fields_ if name != "pad"}
+
+
+def gp_server_destroy(server):
+    _check(lib.gp_server_destroy(server))
 
 
 def gp_out_floats(shader_id: int) -> int:

@@ -241,7 +241,7 @@ gp_status make_uniforms(gp_ctx* c, uint32_t shader, const void* blob, uint32_t b
 }
 
 // Enqueues the partition kernels for 'p' (already sized) on the stream.
-gp_status run_partition(gp_ctx* c, Partition& p, const uint32_t* idx, uint64_t num_idx) {
+gp_status run_partition(gp_ctx* c, Partition& p, const uint32_t* idx, uint64_t num_idx, cudaStream_t stream) {
   PartitionArgs a{};
   a.idx = idx;
   a.num_tris = (uint32_t)(num_idx / 3);
@@ -257,7 +257,7 @@ gp_status run_partition(gp_ctx* c, Partition& p, const uint32_t* idx, uint64_t n
   a.starts = p.d_starts;
   a.num_batches = p.d_count;
   a.err = &c->d_rec[kRing].err;  // the record after the draw ring collects partition errors
-  GP_CUDA(c, launch_partition(a, 4, c->stream));
+  GP_CUDA(c, launch_partition(a, 4, stream));
   return GP_OK;
 }
 
@@ -374,7 +374,7 @@ gp_status enqueue_draw(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* v
       gp_status s = size_partition(c, *p, ib->num_indices, true, cfg.max_unique, cfg.max_tris, cfg.segment_tris);
       if (s != GP_OK) return s;
       p->idx = ib->d_indices;
-      s = run_partition(c, *p, ib->d_indices, ib->num_indices);
+      s = run_partition(c, *p, ib->d_indices, ib->num_indices, c->stream);
       if (s != GP_OK) return s;
     }
     a.starts = p->d_starts;
@@ -609,7 +609,7 @@ gp_status gp_partition(gp_ctx* c, const gp_index_buf* ib, uint64_t* out_handle, 
     return s;
   }
   p.idx = ib->d_indices;
-  s = run_partition(c, p, ib->d_indices, ib->num_indices);
+  s = run_partition(c, p, ib->d_indices, ib->num_indices, c->stream);
   if (s != GP_OK) {
     release_partition(p);
     return s;

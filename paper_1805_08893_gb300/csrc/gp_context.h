@@ -112,7 +112,7 @@ gp_status sync_locked(gp_ctx* c, uint64_t ticket, uint32_t timeout_ms);
 gp_status make_uniforms(gp_ctx* c, uint32_t shader, const void* blob, uint32_t bytes, Uniforms& u);
 gp_status size_partition(gp_ctx* c, Partition& p, uint64_t num_idx, bool reuse_alloc, uint32_t max_unique,
                          uint32_t max_tris, uint32_t segment_tris);
-gp_status run_partition(gp_ctx* c, Partition& p, const uint32_t* idx, uint64_t num_idx);
+gp_status run_partition(gp_ctx* c, Partition& p, const uint32_t* idx, uint64_t num_idx, cudaStream_t stream);
 gp_status check_index_buf(gp_ctx* c, const gp_index_buf* ib);
 gp_status check_draw(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* vb, uint32_t shader,
                      const gp_out_buf* ob);

@@ -211,7 +211,8 @@ gp_status frame_create_locked(gp_ctx* c, const gp_draw_desc* draws, uint32_t n, 
                               c->cfg.segment_tris)) != GP_OK)
         return abort(s);
       p.idx = d.index_buf.d_indices;
-      if (T && (s = run_partition(c, p, d.index_buf.d_indices, d.index_buf.num_indices)) != GP_OK) return abort(s);
+      if (T && (s = run_partition(c, p, d.index_buf.d_indices, d.index_buf.num_indices, c->stream)) != GP_OK)
+        return abort(s);
       a.starts = p.d_starts;
       a.num_batches_dev = p.d_count;
     }
