@@ -126,12 +126,15 @@ class GpError(RuntimeError):
 
 
 def library_path() -> str:
-    return _build.LIB
+    return os.environ.get("GP_LIBRARY") or _build.LIB
 
 
 def _load():
-    path = _build.LIB
-    if not os.path.exists(path) or os.environ.get("GP_BUILD_ON_IMPORT", "1") == "1":
+    """Loads libgp.so, building it first if it is missing or stale.
+    GP_LIBRARY=<path> loads that build of the library instead."""
+    path = os.environ.get("GP_LIBRARY") or _build.LIB
+    if not os.environ.get("GP_LIBRARY") and (not os.path.exists(path) or
+                                              os.environ.get("GP_BUILD_ON_IMPORT", "1") == "1"):
         _build.build()
     L = ctypes.CDLL(path)
     P, U64, U32, I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int

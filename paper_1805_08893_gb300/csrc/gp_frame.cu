@@ -1,7 +1,7 @@
 // Multi-draw frame: every draw call of a frame in one persistent launch.
 //
 // The draws' batches are cut into work items.  Blocks of 256 threads pull
-// items from a global counter.  An item belongs to one draw and is split
+// chunks of consecutive items from a global counter.  An item belongs to one draw and is split
 // among the block's thread groups of that draw's size G (threads per group,
 // chosen per draw; named barriers keep the groups independent):
 //   naive -- one group of 256 threads, one triangle per thread (Section 3.3);
@@ -77,8 +77,8 @@ __device__ __forceinline__ void store_staged(float* dst, const float* src, uint3
 }
 
 template <int SH>
-__device__ __forceinline__ void frame_naive(const FrameDraw& D, uint32_t b, unsigned char* slices,
-                                            const float* palette, unsigned long long& inv, unsigned long long& nbat) {
+__device__ __noinline__ uint2 frame_naive(const FrameDraw& D, uint32_t b, unsigned char* slices,
+                                          const float* palette) {
   constexpr int K = ShaderTraits<SH>::K;
   constexpr int F = 3 * K;
   const DrawArgs& a = D.a;
@@ -86,13 +86,13 @@ __device__ __forceinline__ void frame_naive(const FrameDraw& D, uint32_t b, unsi
   float* stage = reinterpret_cast<float*>(slices) + warp * (32 * F);
   const uint32_t tb0 = b * kFrameThreads;
   const uint32_t ntb = min(kFrameThreads, a.num_tris - tb0);
+  uint2 r = make_uint2(0, 0);
   if (tid == 0) {
-    inv += 3ull * ntb;
-    nbat += 1;
+    r = make_uint2(3u * ntb, 1u);
     if (a.batch_inv != nullptr && b < a.batch_cap) a.batch_inv[b] = 3u * ntb;
   }
   const uint32_t tw0 = tb0 + warp * 32;
-  if (tw0 >= a.num_tris) return;
+  if (tw0 >= a.num_tris) return r;
   const uint32_t ntw = min(32u, a.num_tris - tw0);
   const uint32_t t = tw0 + lane;
   if (lane < ntw) {
@@ -108,28 +108,27 @@ __device__ __forceinline__ void frame_naive(const FrameDraw& D, uint32_t b, unsi
   }
   __syncwarp();
   store_staged(a.out + (size_t)tw0 * F, stage, 0, ntw * F, lane, 32);
+  return r;
 }
 
 template <int SH>
-__device__ __forceinline__ void frame_warp(const FrameDraw& D, uint32_t item, unsigned char* slices,
-                                           const float* palette, unsigned long long& inv, unsigned long long& nbat) {
+__device__ __noinline__ uint2 frame_warp(const FrameDraw& D, uint32_t item, unsigned char* slices,
+                                         const float* palette) {
   const DrawArgs& a = D.a;
   const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
   const uint32_t j = item * (kFrameThreads / 32) + warp;
-  if (j >= D.num_batches) return;
+  if (j >= D.num_batches) return make_uint2(0, 0);
   const uint32_t b = D.batch_begin + j;
   unsigned char* wp = slices + warp * WarpSmem<SH>::per_warp_bytes(3u * a.static_batch_tris);
   const uint32_t n = warp_vote_batch<SH>(a, *D.u, palette, b, wp, lane);
-  if (lane == 0) {
-    inv += n;
-    nbat += 1;
-    if (a.batch_inv != nullptr && b < a.batch_cap) a.batch_inv[b] = n;
-  }
+  if (lane != 0) return make_uint2(0, 0);
+  if (a.batch_inv != nullptr && b < a.batch_cap) a.batch_inv[b] = n;
+  return make_uint2(n, 1u);
 }
 
 template <int METHOD, int SH>
-__device__ __forceinline__ void frame_group(const FrameDraw& D, uint32_t item, unsigned char* slices,
-                                            const float* palette, unsigned long long& inv, unsigned long long& nbat) {
+__device__ __noinline__ uint2 frame_group(const FrameDraw& D, uint32_t item, unsigned char* slices,
+                                          const float* palette) {
   constexpr int DEDUP = METHOD == kFrameSort ? DEDUP_SORT : (METHOD == kFrameHash ? DEDUP_HASH : DEDUP_PHASH);
   constexpr int K = ShaderTraits<SH>::K;
   constexpr int KS = ShaderTraits<SH>::KS;
@@ -138,7 +137,7 @@ __device__ __forceinline__ void frame_group(const FrameDraw& D, uint32_t item, u
   const uint32_t G = D.group;
   const uint32_t g = threadIdx.x / G, gt = threadIdx.x % G;
   const uint32_t j = item * (kFrameThreads / G) + g;
-  if (j >= D.num_batches) return;  // the whole group is idle; its barrier is not used
+  if (j >= D.num_batches) return make_uint2(0, 0);  // the whole group is idle; its barrier is not used
   const uint32_t b = D.batch_begin + j;
   const GroupSync sync{g + 1, G};
   const FrameSlice L = frame_slice(METHOD, K, KS, a.max_batch_idx, a.ucap, a.hash_slots, a.sort_n, G);
@@ -168,7 +167,7 @@ __device__ __forceinline__ void frame_group(const FrameDraw& D, uint32_t item, u
   const uint32_t n = 3 * (t1 - t0);
   if (n > a.max_batch_idx) {  // cannot happen with a consistent configuration
     if (gt == 0) atomicOr(a.err, EBIT_CAPACITY);
-    return;
+    return make_uint2(0, 0);
   }
   for (uint32_t i = gt; i < n; i += G) win[i] = __ldg(a.idx + 3 * t0 + i);
   if (DEDUP != DEDUP_SORT)
@@ -183,69 +182,77 @@ __device__ __forceinline__ void frame_group(const FrameDraw& D, uint32_t item, u
   fill_stage<DEDUP, SH>(a, S, stage + pad, 0, n, U, 3ull * t0, gt, G, pad == 0);
   sync();
   store_staged(a.out + g0, stage, pad, (t1 - t0) * F, gt, G);
-  if (gt == 0) {
-    inv += U;
-    nbat += 1;
-    if (a.batch_inv != nullptr && b < a.batch_cap) a.batch_inv[b] = U;
+  if (gt != 0) return make_uint2(0, 0);
+  if (a.batch_inv != nullptr && b < a.batch_cap) a.batch_inv[b] = U;
+  return make_uint2(U, 1u);
+}
+
+// Per-method bodies are separate (not inlined) functions, each with its own
+// register allocation, so the heaviest path does not make every path spill.
+template <int SH>
+__device__ __forceinline__ uint2 frame_item(const FrameDraw& D, uint32_t item, unsigned char* slices,
+                                            const float* palette) {
+  switch (D.method) {
+    case kFrameNaive: return frame_naive<SH>(D, D.batch_begin + item, slices, palette);
+    case kFrameWarp: return frame_warp<SH>(D, item, slices, palette);
+    case kFrameSort: return frame_group<kFrameSort, SH>(D, item, slices, palette);
+    case kFrameHash: return frame_group<kFrameHash, SH>(D, item, slices, palette);
+    default: return frame_group<kFramePHash, SH>(D, item, slices, palette);
   }
 }
 
-template <int SH>
-__device__ __forceinline__ void frame_item(const FrameDraw& D, uint32_t item, unsigned char* slices,
-                                           const float* palette, unsigned long long& inv, unsigned long long& nbat) {
-  switch (D.method) {
-    case kFrameNaive: frame_naive<SH>(D, D.batch_begin + item, slices, palette, inv, nbat); break;
-    case kFrameWarp: frame_warp<SH>(D, item, slices, palette, inv, nbat); break;
-    case kFrameSort: frame_group<kFrameSort, SH>(D, item, slices, palette, inv, nbat); break;
-    case kFrameHash: frame_group<kFrameHash, SH>(D, item, slices, palette, inv, nbat); break;
-    default: frame_group<kFramePHash, SH>(D, item, slices, palette, inv, nbat); break;
-  }
-}
+// Work items are handed out in chunks of kFrameChunk consecutive items per
+// atomic, so the counter's latency is paid once per chunk and consecutive
+// items usually belong to the same draw; item_draw[item] names an item's
+// draw, and the draw's descriptor is copied to shared memory only when it
+// changes.
+constexpr uint32_t kFrameChunk = 8;
 
 __global__ void __launch_bounds__(kFrameThreads, 3) frame_kernel(const FrameDraw* __restrict__ draws,
-                                                                 uint32_t num_draws, uint32_t total_items,
-                                                                 uint32_t* work, unsigned long long* counters) {
+                                                                 const uint32_t* __restrict__ item_draw,
+                                                                 uint32_t total_items, uint32_t* work,
+                                                                 unsigned long long* counters) {
   extern __shared__ __align__(128) unsigned char smem[];
   float* palette = reinterpret_cast<float*>(smem);
   unsigned char* slices = smem + 768 * 4;
-  __shared__ uint32_t s_item;
+  __shared__ uint32_t s_base;
   __shared__ __align__(16) FrameDraw s_draw;  // the current item's draw, read from shared memory
   unsigned long long inv = 0, nbat = 0;
   uint32_t pal_draw = 0xFFFFFFFFu, cur_draw = 0xFFFFFFFFu;
   for (;;) {
-    if (threadIdx.x == 0) s_item = atomicAdd(work, 1u);
+    if (threadIdx.x == 0) s_base = atomicAdd(work, kFrameChunk);
     __syncthreads();
-    const uint32_t item = s_item;
-    if (item >= total_items) break;
-    // the draw whose item range holds this item (item_begin is increasing)
-    uint32_t lo = 0, hi = num_draws;
-    while (hi - lo > 1) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (draws[mid].item_begin <= item) lo = mid;
-      else hi = mid;
+    const uint32_t base = s_base;
+    if (base >= total_items) break;
+    const uint32_t end = min(base + kFrameChunk, total_items);
+    for (uint32_t item = base; item < end; ++item) {
+      const uint32_t d = __ldg(item_draw + item);  // uniform across the block
+      if (d != cur_draw) {
+        constexpr uint32_t kWords = sizeof(FrameDraw) / 4;
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(draws + d);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&s_draw);
+        for (uint32_t i = threadIdx.x; i < kWords; i += blockDim.x) dst[i] = src[i];
+        cur_draw = d;
+        __syncthreads();
+      }
+      const FrameDraw& D = s_draw;
+      if (D.shader == 1 && pal_draw != d) {
+        for (uint32_t i = threadIdx.x; i < 768; i += blockDim.x) palette[i] = D.u->palette[i];
+        pal_draw = d;
+        __syncthreads();
+      }
+      const uint32_t local = item - D.item_begin;
+      uint2 r;
+      switch (D.shader) {
+        case 0: r = frame_item<0>(D, local, slices, palette); break;
+        case 1: r = frame_item<1>(D, local, slices, palette); break;
+        case 2: r = frame_item<2>(D, local, slices, palette); break;
+        default: r = frame_item<3>(D, local, slices, palette); break;
+      }
+      inv += r.x;
+      nbat += r.y;
+      __syncthreads();  // the slices (and possibly the descriptor) are reused by the next item
     }
-    if (cur_draw != lo) {  // uniform: every thread found the same draw
-      constexpr uint32_t kWords = sizeof(FrameDraw) / 4;
-      const uint32_t* src = reinterpret_cast<const uint32_t*>(draws + lo);
-      uint32_t* dst = reinterpret_cast<uint32_t*>(&s_draw);
-      for (uint32_t i = threadIdx.x; i < kWords; i += blockDim.x) dst[i] = src[i];
-      cur_draw = lo;
-      __syncthreads();
-    }
-    const FrameDraw& D = s_draw;
-    if (D.shader == 1 && pal_draw != lo) {
-      for (uint32_t i = threadIdx.x; i < 768; i += blockDim.x) palette[i] = D.u->palette[i];
-      pal_draw = lo;
-      __syncthreads();
-    }
-    const uint32_t local = item - D.item_begin;
-    switch (D.shader) {
-      case 0: frame_item<0>(D, local, slices, palette, inv, nbat); break;
-      case 1: frame_item<1>(D, local, slices, palette, inv, nbat); break;
-      case 2: frame_item<2>(D, local, slices, palette, inv, nbat); break;
-      default: frame_item<3>(D, local, slices, palette, inv, nbat); break;
-    }
-    __syncthreads();  // the slices are carved anew for the next item
   }
   // per-thread partial counts (group leaders, warp leaders) into the record
   if (inv) atomicAdd(counters + CNT_INVOCATIONS, inv);
@@ -264,12 +271,12 @@ int frame_blocks_per_sm() {
   return nb;
 }
 
-cudaError_t launch_frame(const FrameDraw* d_draws, uint32_t num_draws, uint32_t total_items, uint32_t* d_work,
-                         unsigned long long* d_counters, int grid, cudaStream_t s) {
+cudaError_t launch_frame(const FrameDraw* d_draws, const uint32_t* d_item_draw, uint32_t total_items,
+                         uint32_t* d_work, unsigned long long* d_counters, int grid, cudaStream_t s) {
   const size_t smem = frame_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(frame_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  frame_kernel<<<grid, kFrameThreads, smem, s>>>(d_draws, num_draws, total_items, d_work, d_counters);
+  frame_kernel<<<grid, kFrameThreads, smem, s>>>(d_draws, d_item_draw, total_items, d_work, d_counters);
   return cudaGetLastError();
 }
 

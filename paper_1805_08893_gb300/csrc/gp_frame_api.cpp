@@ -24,6 +24,7 @@ struct gp_frame {
   std::vector<Uniforms> h_uni;
   std::vector<Partition> parts;  // one per draw (empty for static draws)
   FrameDraw* d_draws = nullptr;
+  uint32_t* d_item_draw = nullptr;  // work item -> draw
   Uniforms* d_uni = nullptr;
   uint32_t* d_work = nullptr;
   DevRec* d_rec = nullptr;
@@ -130,6 +131,7 @@ void free_frame(gp_frame* f) {
   if (f->graph) cudaGraphDestroy(f->graph);
   if (f->cap_stream) cudaStreamDestroy(f->cap_stream);
   if (f->d_draws) cudaFree(f->d_draws);
+  if (f->d_item_draw) cudaFree(f->d_item_draw);
   if (f->d_uni) cudaFree(f->d_uni);
   if (f->d_work) cudaFree(f->d_work);
   if (f->d_rec) cudaFree(f->d_rec);
@@ -243,6 +245,15 @@ gp_status frame_create_locked(gp_ctx* c, const gp_draw_desc* draws, uint32_t n, 
     f->cfg[i].batches = D.num_batches;
   }
   f->total_items = item;
+  if (item) {
+    std::vector<uint32_t> h_item_draw(item);
+    for (uint32_t i = 0; i < n; ++i)
+      for (uint32_t j = 0; j < f->h_draws[i].items; ++j) h_item_draw[f->h_draws[i].item_begin + j] = i;
+    if ((e = cudaMalloc(&f->d_item_draw, sizeof(uint32_t) * item)) != cudaSuccess ||
+        (e = cudaMemcpy(f->d_item_draw, h_item_draw.data(), sizeof(uint32_t) * item, cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+      return abort(cuda_fail(c, e, "item table"));
+  }
   if (n) {
     if ((e = cudaMalloc(&f->d_draws, sizeof(FrameDraw) * n)) != cudaSuccess ||
         (e = cudaMalloc(&f->d_uni, sizeof(Uniforms) * n)) != cudaSuccess)
@@ -262,8 +273,9 @@ gp_status frame_create_locked(gp_ctx* c, const gp_draw_desc* draws, uint32_t n, 
     return abort(cuda_fail(c, e, "cudaStreamBeginCapture"));
   cudaError_t e1 = cudaMemsetAsync(f->d_work, 0, 16, f->cap_stream);
   cudaError_t e2 = cudaMemsetAsync(f->d_rec, 0, sizeof(DevRec), f->cap_stream);
-  cudaError_t e3 = n ? launch_frame(f->d_draws, n, f->total_items, f->d_work, f->d_rec->cnt, f->grid, f->cap_stream)
-                     : cudaSuccess;
+  cudaError_t e3 = f->total_items ? launch_frame(f->d_draws, f->d_item_draw, f->total_items, f->d_work,
+                                                f->d_rec->cnt, f->grid, f->cap_stream)
+                                  : cudaSuccess;
   e = cudaStreamEndCapture(f->cap_stream, &f->graph);
   if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e != cudaSuccess)
     return abort(cuda_fail(c, e3 != cudaSuccess ? e3 : (e != cudaSuccess ? e : (e1 != cudaSuccess ? e1 : e2)),

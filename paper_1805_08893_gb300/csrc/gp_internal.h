@@ -128,8 +128,9 @@ uint32_t frame_slice_bytes(int method, int shader, uint32_t max_idx, uint32_t uc
                            uint32_t group, uint32_t batch_idx);
 size_t frame_smem_bytes();
 int frame_blocks_per_sm();
-cudaError_t launch_frame(const FrameDraw* d_draws, uint32_t num_draws, uint32_t total_items, uint32_t* d_work,
-                         unsigned long long* d_counters, int grid, cudaStream_t s);
+// item_draw[i]: the entry of draws[] that work item i belongs to.
+cudaError_t launch_frame(const FrameDraw* d_draws, const uint32_t* d_item_draw, uint32_t total_items,
+                         uint32_t* d_work, unsigned long long* d_counters, int grid, cudaStream_t s);
 
 // Sets the calling thread's context-free error text (gp_last_error(NULL)).
 void set_thread_error(const char* msg);

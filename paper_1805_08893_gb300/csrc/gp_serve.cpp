@@ -72,6 +72,8 @@ struct StepSlot {
   FrameDraw* h_draws = nullptr;  // pinned
   Uniforms* h_uni = nullptr;     // pinned staging for uniform uploads
   FrameDraw* d_draws = nullptr;
+  uint32_t* h_item_draw = nullptr;  // pinned: work item -> entry
+  uint32_t* d_item_draw = nullptr;
   uint32_t* d_work = nullptr;
   DevRec* d_rec = nullptr;
   DevRec* h_rec = nullptr;       // pinned
@@ -329,6 +331,7 @@ bool launch_step(gp_server* s, StepSlot& st) {
     const uint32_t per = D.method == kFrameNaive ? 1u : (D.method == kFrameWarp ? kFrameThreads / 32 : kFrameThreads / D.group);
     D.items = (take + per - 1) / per;
     D.item_begin = items;
+    for (uint32_t j = 0; j < D.items; ++j) st.h_item_draw[items + j] = n;
     items += D.items;
     if (!r.uploaded) {
       st.h_uni[nuni] = r.uni;
@@ -352,10 +355,11 @@ bool launch_step(gp_server* s, StepSlot& st) {
     if (&o != &st) cudaStreamWaitEvent(q, o.ev_uni, 0);
   cudaEventRecord(st.ev0, q);
   cudaMemcpyAsync(st.d_draws, st.h_draws, sizeof(FrameDraw) * n, cudaMemcpyHostToDevice, q);
+  cudaMemcpyAsync(st.d_item_draw, st.h_item_draw, sizeof(uint32_t) * items, cudaMemcpyHostToDevice, q);
   cudaMemsetAsync(st.d_work, 0, 16, q);
   cudaMemsetAsync(st.d_rec, 0, sizeof(DevRec), q);
   const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)s->ctx->sms * s->frame_bpsm, items));
-  cudaError_t e = launch_frame(st.d_draws, n, items, st.d_work, st.d_rec->cnt, grid, q);
+  cudaError_t e = launch_frame(st.d_draws, st.d_item_draw, items, st.d_work, st.d_rec->cnt, grid, q);
   cudaMemcpyAsync(st.h_rec, st.d_rec, sizeof(DevRec), cudaMemcpyDeviceToHost, q);
   cudaEventRecord(st.ev1, q);
   if (e != cudaSuccess) s->last_error = GP_ERR_CUDA;
@@ -430,6 +434,8 @@ void free_server(gp_server* s) {
     if (st.h_uni) cudaFreeHost(st.h_uni);
     if (st.h_rec) cudaFreeHost(st.h_rec);
     if (st.d_draws) cudaFree(st.d_draws);
+    if (st.h_item_draw) cudaFreeHost(st.h_item_draw);
+    if (st.d_item_draw) cudaFree(st.d_item_draw);
     if (st.d_work) cudaFree(st.d_work);
     if (st.d_rec) cudaFree(st.d_rec);
   }
@@ -512,7 +518,7 @@ gp_status gp_server_create(gp_ctx* c, const gp_serve_config* cfg_in, gp_server**
   k.max_unique = cfg.max_unique;
   k.max_tris = cfg.max_tris;
   k.threads_per_group = cfg.threads_per_group;
-  if (cfg.variant < GP_NAIVE || cfg.variant > GP_AUTO || cfg.streams > 16) {
+  if (cfg.variant < GP_NAIVE || cfg.variant > GP_AUTO || cfg.streams > 16 || cfg.step_max_batches > (1u << 20)) {
     delete s;
     return GP_ERR_INVALID;
   }
@@ -550,6 +556,8 @@ gp_status gp_server_create(gp_ctx* c, const gp_serve_config* cfg_in, gp_server**
     if ((e = cudaMallocHost(&st.h_uni, sizeof(Uniforms) * kStepMaxEntries)) != cudaSuccess) break;
     if ((e = cudaMallocHost(&st.h_rec, sizeof(DevRec))) != cudaSuccess) break;
     if ((e = cudaMalloc(&st.d_draws, sizeof(FrameDraw) * kStepMaxEntries)) != cudaSuccess) break;
+    if ((e = cudaMallocHost(&st.h_item_draw, sizeof(uint32_t) * cfg.step_max_batches)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&st.d_item_draw, sizeof(uint32_t) * cfg.step_max_batches)) != cudaSuccess) break;
     if ((e = cudaMalloc(&st.d_work, 16)) != cudaSuccess) break;
     if ((e = cudaMalloc(&st.d_rec, sizeof(DevRec))) != cudaSuccess) break;
   }
