@@ -23,6 +23,9 @@ using namespace gp;
 
 namespace {
 thread_local std::string g_create_error;
+// Shared memory a block of the single-draw reuse kernel should stay within,
+// so that four blocks fit on an SM (227 KB each, 1 KB reserved per block).
+constexpr size_t kBatchedSmemTarget = 55 * 1024;
 }  // namespace
 
 namespace gp {
@@ -390,14 +393,22 @@ gp_status enqueue_draw(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* v
   }
   if (cfg.hash_slots && cfg.hash_slots < a.ucap)
     return fail(c, GP_ERR_INVALID, "hash_slots must be at least the unique-vertex capacity of a batch");
-  a.hash_slots = cfg.hash_slots ? cfg.hash_slots : next_pow2(2 * a.ucap);
+  // default: at least 2x the unique capacity, and 4x up to 1024 slots (fewer
+  // collisions, so shorter probe sequences, where the table stays small)
+  a.hash_slots = cfg.hash_slots ? cfg.hash_slots : std::max(next_pow2(2 * a.ucap), std::min(next_pow2(4 * a.ucap), 1024u));
   a.hash_slots = std::max(a.hash_slots, next_pow2(threads));
+  if (a.hash_slots > 32u * threads)  // each thread numbers a run of at most 32 slots
+    return fail(c, GP_ERR_UNSUPPORTED, "hash_slots may be at most 32 x threads_per_group");
   a.hash_bits = log2u(a.hash_slots);
   a.sort_n = next_pow2(a.max_batch_idx);
-  a.out_chunk = (a.max_batch_idx + 2) / 3;  // the whole batch in one bulk store
+  // staging for the output: the whole batch while four blocks fit on an SM,
+  // else the largest power-of-two fraction of it that lets them
+  a.out_chunk = (a.max_batch_idx + 2) / 3;
+  while (a.out_chunk > 32 && batched_smem_bytes(dedup, (int)shader, a, (int)threads) > kBatchedSmemTarget)
+    a.out_chunk = (a.out_chunk + 1) / 2;
   if (const char* oc = std::getenv("GP_OUT_CHUNK")) {  // tuning override
     const long v = std::strtol(oc, nullptr, 10);
-    if (v > 0) a.out_chunk = std::min<uint32_t>((uint32_t)v, a.out_chunk);
+    if (v > 0) a.out_chunk = std::min<uint32_t>((uint32_t)v, (a.max_batch_idx + 2) / 3);
   }
   const size_t smem = batched_smem_bytes(dedup, (int)shader, a, (int)threads);
   if (smem > 227 * 1024)

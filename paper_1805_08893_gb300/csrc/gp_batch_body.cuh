@@ -1,9 +1,12 @@
 // The per-batch work of the reuse methods, shared by the single-draw kernel
 // (one thread block per batch) and the multi-draw frame kernel (one thread
 // group per batch, several groups per block):
-//   * dedup_and_shade -- find the batch's unique indices (Algorithm 2 sort,
-//     Algorithm 3 hash, Section 3.4 parallel hash) and shade each once;
-//   * fill_stage     -- write a run of assembled triangles, in input order,
+//   * dedup           -- find the batch's unique indices (Algorithm 2 sort,
+//     Algorithm 3 hash, Section 3.4 parallel hash); each warp hands its new
+//     vertices to a consumer as it finds them (ShadeQueue shades them at
+//     once), or (hash/phash without ranks) leaves the numbering to the caller;
+//   * dedup_and_shade -- dedup with ShadeQueue;
+//   * fill_stage      -- write a run of assembled triangles, in input order,
 //     into a shared staging buffer.
 // 'tid'/'NT' are the thread's index in and the size of its group; 'sync' is
 // the group barrier (__syncthreads for a whole block, a named barrier for a
@@ -14,8 +17,7 @@
 
 namespace gp {
 
-constexpr int kIdsPerRound = 4;  // indices a thread handles before its warp shades the new ones
-constexpr uint16_t kNoRank = 0xFFFFu;
+constexpr int kIdsPerRound = 4;  // indices a thread inserts before its warp takes ranks for the new ones
 
 struct BlockSync {
   __device__ __forceinline__ void operator()() const { __syncthreads(); }
@@ -38,7 +40,6 @@ struct BatchSmem {
   uint16_t* dense;              // hash: slot -> rank
   uint32_t* uniq;               // rank -> vertex id
   float* vsh;                   // rank -> shaded vertex (KS floats)
-  uint16_t* wq;                 // this warp's queue of new ranks (32 * kIdsPerRound)
   uint32_t* ucount;             // unique count of the batch
   uint32_t* wsum;               // per-warp totals for the sort's scan (>= NT/32 words)
 };
@@ -61,43 +62,87 @@ __device__ __forceinline__ void store_shaded(float* vsh, uint32_t k, const float
   }
 }
 
-// Shades the warp's queue of new vertices (their ranks; the id is uniq[rank])
-// in full-warp passes: two vertices per lane per pass, both loads issued
-// before the math.
+// Shades the new vertices of ranks [rb, re) (ids in uniq; ranks >= ucap
+// were not stored) in full-warp passes: two vertices per lane per pass, both
+// loads issued before the math.
 template <int SH>
-__device__ __forceinline__ void shade_queue(const DrawArgs& a, const Uniforms& u, const float* palette, float* vsh,
-                                            const uint32_t* uniq, const uint16_t* q, uint32_t qn, uint32_t lane) {
-  constexpr int K = ShaderTraits<SH>::K;
-  for (uint32_t e = lane; e < qn; e += 64) {
-    const bool has1 = e + 32 < qn;
-    const uint32_t r0 = q[e], r1 = has1 ? q[e + 32] : kNoRank;
-    const uint32_t id0 = r0 != kNoRank ? uniq[r0] : kInvalidId;
-    const uint32_t id1 = r1 != kNoRank ? uniq[r1] : kInvalidId;
+__device__ __forceinline__ void shade_range(const DrawArgs& a, const Uniforms& u, const float* palette, float* vsh,
+                                            const uint32_t* uniq, uint32_t rb, uint32_t re, uint32_t lane) {
+  re = min(re, a.ucap);
+  for (uint32_t r0 = rb + lane; r0 < re; r0 += 64) {
+    const uint32_t r1 = r0 + 32;
+    const bool has1 = r1 < re;
+    const uint32_t id0 = uniq[r0];
+    const uint32_t id1 = has1 ? uniq[r1] : kInvalidId;
     VertexIn v0, v1;
     const bool ok0 = id0 < a.num_verts, ok1 = id1 < a.num_verts;
     if (ok0) fetch_vertex<SH>(a.verts, a.stride, id0, v0, a.vec8 != 0);
     if (ok1) fetch_vertex<SH>(a.verts, a.stride, id1, v1, a.vec8 != 0);
-    float o[K];
-    if (r0 != kNoRank) {
-      if (ok0) {
-        shade_vertex<SH>(u, palette, v0, o);
-      } else {
+    float o[ShaderTraits<SH>::K];
+    if (ok0) {
+      shade_vertex<SH>(u, palette, v0, o);
+    } else {
 #pragma unroll
-        for (int c = 0; c < K; ++c) o[c] = 0.f;
-        atomicOr(a.err, EBIT_INDEX_RANGE);
-      }
-      store_shaded<SH>(vsh, r0, o);
+      for (int c = 0; c < ShaderTraits<SH>::K; ++c) o[c] = 0.f;
+      atomicOr(a.err, EBIT_INDEX_RANGE);
     }
-    if (r1 != kNoRank) {
+    store_shaded<SH>(vsh, r0, o);
+    if (has1) {
       if (ok1) {
         shade_vertex<SH>(u, palette, v1, o);
       } else {
 #pragma unroll
-        for (int c = 0; c < K; ++c) o[c] = 0.f;
+        for (int c = 0; c < ShaderTraits<SH>::K; ++c) o[c] = 0.f;
         atomicOr(a.err, EBIT_INDEX_RANGE);
       }
       store_shaded<SH>(vsh, r1, o);
     }
+  }
+}
+
+// Bytes of a vertex row the shaders read, copied whole into shared memory by
+// the single-draw kernel (a multiple of 16: the vertex buffer's base and
+// stride are 16-byte aligned).
+template <int SH>
+struct RawTraits {
+  static constexpr uint32_t kBytes = ShaderTraits<SH>::kSkin ? 64u : 32u;
+  static constexpr uint32_t kChunks = kBytes / 16u;
+};
+
+// Consumers of new vertices: called by all lanes of a warp after __syncwarp
+// with the range [rb, re) of ranks this warp has just created; S.uniq[rank]
+// holds the vertex id for every rank < ucap (ranks >= ucap are a flagged
+// capacity error and were not stored).
+template <int SH>
+struct ShadeQueue {
+  const DrawArgs& a;
+  const Uniforms& u;
+  const float* palette;
+  float* vsh;
+  const uint32_t* uniq;
+  __device__ __forceinline__ void operator()(uint32_t rb, uint32_t re, uint32_t lane) const {
+    shade_range<SH>(a, u, palette, vsh, uniq, rb, re, lane);
+  }
+};
+
+// For a caller that consumes the new vertices after dedup returns.
+struct NoConsume {
+  __device__ __forceinline__ void operator()(uint32_t, uint32_t, uint32_t) const {}
+};
+
+// Reads a vertex row copied into shared memory (16-byte aligned).
+template <int SH>
+__device__ __forceinline__ void load_raw(const unsigned char* row, VertexIn& v) {
+  const float4* p = reinterpret_cast<const float4*>(row);
+  const float4 x = p[0], y = p[1];
+  v.px = x.x; v.py = x.y; v.pz = x.z;
+  v.nx = x.w; v.ny = y.x; v.nz = y.y;
+  if (ShaderTraits<SH>::kSkin) {
+    const float4 z = p[2], w = p[3];
+    v.bones = __float_as_uint(z.x);
+    v.w0 = z.y; v.w1 = z.z; v.w2 = z.w; v.w3 = w.x;
+  } else {
+    v.bones = 0; v.w0 = v.w1 = v.w2 = v.w3 = 0.f;
   }
 }
 
@@ -187,16 +232,19 @@ __device__ __forceinline__ void bitonic_sort(unsigned long long* keys, uint32_t 
   sync();
 }
 
-// Finds the unique indices of ids[0..n) and shades each once into S.vsh.
-// On return (after a group barrier the caller issues) *S.ucount holds the
-// unique count U, S.uniq[0..U) the ids, and S.map (with S.dense for hash)
-// each corner's rank.  The hash table must be empty on entry; it is left
+// Finds the unique indices of ids[0..n) and passes each new one, once, to
+// 'consume' (see ShadeQueue).  On return (after a group barrier
+// the caller issues) *S.ucount holds the unique count U, S.uniq[0..U) the
+// ids, and S.map each corner's rank (sort) or hash slot (hash/phash; the
+// rank is S.dense[slot]).  The hash table must be empty on entry; it is left
 // filled (the caller clears it after the barrier).  *S.ucount must be 0 on
 // entry for hash/phash.
-template <int DEDUP, int SH, class Sync>
-__device__ __forceinline__ void dedup_and_shade(const DrawArgs& a, const Uniforms& u, const float* palette,
-                                                const BatchSmem& S, const uint32_t* ids, uint32_t n, uint32_t tid,
-                                                uint32_t NT, Sync sync) {
+// RANKS == false (hash/phash only): the table and S.map (slots) are all it
+// produces -- no ranks, no uniq, no consume; the caller numbers the filled
+// slots itself (compact_table in the single-draw kernel).
+template <int DEDUP, bool RANKS, class Sync, class Consume>
+__device__ __forceinline__ void dedup(const DrawArgs& a, const BatchSmem& S, const uint32_t* ids, uint32_t n,
+                                      uint32_t tid, uint32_t NT, Sync sync, const Consume& consume) {
   const uint32_t lane = lane_id(), warp = tid >> 5;
   if (DEDUP == DEDUP_SORT) {
     // --- Algorithm 2: sort (id, position), tail flags, exclusive prefix sum
@@ -224,45 +272,32 @@ __device__ __forceinline__ void dedup_and_shade(const DrawArgs& a, const Uniform
     uint32_t r = inc - cnt;
     for (uint32_t w = 0; w < warp; ++w) r += S.wsum[w];
     if (tid == NT - 1) *S.ucount = r + cnt;
-    // walk the run in rounds of kIdsPerRound elements (ipt is the same for
-    // every thread, so the warp's ballots line up); tails go to the warp's
-    // shading queue
-    for (uint32_t off = 0; off < ipt; off += kIdsPerRound) {
-      uint32_t qn = 0;
-#pragma unroll
-      for (int q = 0; q < kIdsPerRound; ++q) {
-        const uint32_t i = lo + off + q;
-        bool tail = false;
-        uint32_t id = 0;
-        if (off + q < ipt && i < hi) {
-          id = (uint32_t)(S.keys[i] >> 32);
-          S.map[(uint32_t)(S.keys[i] & 0xFFFFu)] = (uint16_t)r;
-          tail = (i == n - 1) || id != (uint32_t)(S.keys[i + 1] >> 32);
-        }
-        const uint32_t tm = __ballot_sync(kFull, tail);
-        if (tail) {
-          uint16_t rk = (uint16_t)r;
-          if (r < a.ucap) {
-            S.uniq[r] = id;
-          } else {
-            atomicOr(a.err, EBIT_CAPACITY);
-            rk = kNoRank;
-          }
-          S.wq[qn + __popc(tm & lanemask_lt())] = rk;
-          ++r;
-        }
-        qn += __popc(tm);
+    // the warp's ranks are contiguous: lane 0's first to lane 31's last
+    const uint32_t rb = __shfl_sync(kFull, r, 0), re = __shfl_sync(kFull, r + cnt, 31);
+    for (uint32_t i = lo; i < hi; ++i) {
+      const unsigned long long key = S.keys[i];
+      const uint32_t id = (uint32_t)(key >> 32);
+      S.map[(uint32_t)(key & 0xFFFFu)] = (uint16_t)r;
+      if (i == n - 1 || id != (uint32_t)(S.keys[i + 1] >> 32)) {  // tail of an id's group
+        if (r < a.ucap) S.uniq[r] = id;
+        else atomicOr(a.err, EBIT_CAPACITY);
+        ++r;
       }
-      __syncwarp();
-      shade_queue<SH>(a, u, palette, S.vsh, S.uniq, S.wq, qn, lane);
-      __syncwarp();
     }
+    __syncwarp();
+    consume(rb, re, lane);
+    __syncwarp();
   } else {
-    // --- Algorithm 3 / Section 3.4: insert; the thread storing a new id
-    // takes its rank, and the warp shades its new ids together
+    // --- Algorithm 3 / Section 3.4: every index tries to store its id in its
+    // home slot with atomicCAS and probes on after a collision (hash: linear,
+    // one slot at a time; phash: up to probe_k slots alone, then 32
+    // consecutive slots at a time with the whole warp).  A thread handles
+    // kIdsPerRound indices one after another; the other warps of the SM hide
+    // the atomics' latency.
     const uint32_t mask = a.hash_slots - 1;
     for (uint32_t rbase = 0; rbase < n; rbase += kIdsPerRound * NT) {
-      uint32_t qn = 0;  // the warp's queue of new ranks
+      uint32_t idq[kIdsPerRound], hq[kIdsPerRound], prevq[kIdsPerRound];
+      uint32_t newbits = 0;  // bit q: this thread stored idq[q]
 #pragma unroll
       for (int q = 0; q < kIdsPerRound; ++q) {
         const uint32_t i = rbase + q * NT + tid;
@@ -273,34 +308,34 @@ __device__ __forceinline__ void dedup_and_shade(const DrawArgs& a, const Uniform
         bool is_new = false;
         if (DEDUP == DEDUP_HASH) {
           if (active) {
-            for (uint32_t probes = 0;; ++probes) {
-              const uint32_t prev = atomicCAS(&S.table[h], kEmpty, id);
-              if (prev == kEmpty) {
-                is_new = true;
-                break;
-              }
-              if (prev == id) break;
-              h = (h + 1) & mask;
-              if (probes > a.hash_slots) {  // table full: cannot happen within capacity
+            uint32_t prev = atomicCAS(&S.table[h], kEmpty, id);
+            for (uint32_t probes = 1; prev != kEmpty && prev != id; ++probes) {
+              if (probes >= a.hash_slots) {  // table full: cannot happen within capacity
                 atomicOr(a.err, EBIT_CAPACITY);
                 h = 0;
                 break;
               }
+              h = (h + 1) & mask;
+              prev = atomicCAS(&S.table[h], kEmpty, id);
             }
+            is_new = prev == kEmpty;
           }
         } else {
-          bool placed = !active;
-          for (uint32_t p = 0; p < a.probe_k && !placed; ++p) {
+          bool pending = active;
+          for (uint32_t p = 0; p < a.probe_k && pending; ++p) {
             const uint32_t prev = atomicCAS(&S.table[h], kEmpty, id);
-            if (prev == kEmpty) is_new = true;
-            if (prev == kEmpty || prev == id) placed = true;
-            else h = (h + 1) & mask;
+            if (prev == kEmpty || prev == id) {
+              pending = false;
+              is_new = prev == kEmpty;
+            } else {
+              h = (h + 1) & mask;
+            }
           }
-          uint32_t pending = __ballot_sync(kFull, !placed);
-          while (pending) {
-            const uint32_t leader = __ffs(pending) - 1;
+          uint32_t left = __ballot_sync(kFull, pending);
+          while (left) {
+            const uint32_t leader = __ffs(left) - 1;
             const uint32_t lid = __shfl_sync(kFull, id, leader);
-            uint32_t lh = __shfl_sync(kFull, h, leader);
+            uint32_t lh = __shfl_sync(kFull, h, leader);  // the next slot to probe
             uint32_t found = kEmpty;
             bool fresh = false;
             for (uint32_t guard = 0; found == kEmpty; ++guard) {
@@ -320,12 +355,12 @@ __device__ __forceinline__ void dedup_and_shade(const DrawArgs& a, const Uniform
               if (emp) {
                 const uint32_t fl = __ffs(emp) - 1;
                 const uint32_t cs = (lh + fl) & mask;
-                uint32_t prev = 0;
-                if (lane == fl) prev = atomicCAS(&S.table[cs], kEmpty, lid);
-                prev = __shfl_sync(kFull, prev, fl);
-                if (prev == kEmpty || prev == lid) {
+                uint32_t pv = 0;
+                if (lane == fl) pv = atomicCAS(&S.table[cs], kEmpty, lid);
+                pv = __shfl_sync(kFull, pv, fl);
+                if (pv == kEmpty || pv == lid) {
                   found = cs;
-                  fresh = prev == kEmpty;
+                  fresh = pv == kEmpty;
                 } else {
                   lh = cs;  // the slot was just taken: continue probing from it
                 }
@@ -337,37 +372,58 @@ __device__ __forceinline__ void dedup_and_shade(const DrawArgs& a, const Uniform
               h = found;
               is_new = fresh;
             }
-            pending &= pending - 1;
+            left &= left - 1;
           }
         }
-        // warp-aggregated dense ranks for the new ids
-        const uint32_t newmask = __ballot_sync(kFull, is_new);
-        uint32_t wbase = 0;
-        if (newmask) {
-          const uint32_t leader = __ffs(newmask) - 1;
-          if (lane == leader) wbase = atomicAdd(S.ucount, __popc(newmask));
-          wbase = __shfl_sync(kFull, wbase, leader);
-        }
-        if (is_new) {
-          const uint32_t pos = __popc(newmask & lanemask_lt());
-          const uint32_t rk = wbase + pos;
-          if (rk < a.ucap) {
-            S.dense[h] = (uint16_t)rk;
-            S.uniq[rk] = id;
-            S.wq[qn + pos] = (uint16_t)rk;
-          } else {
-            atomicOr(a.err, EBIT_CAPACITY);
-            S.wq[qn + pos] = kNoRank;
-          }
-        }
-        qn += __popc(newmask);
-        if (active) S.map[i] = (uint16_t)h;
+        if (active && !RANKS) S.map[i] = (uint16_t)h;
+        idq[q] = id;
+        hq[q] = h;
+        newbits |= is_new ? (1u << q) : 0u;
       }
-      __syncwarp();
-      shade_queue<SH>(a, u, palette, S.vsh, S.uniq, S.wq, qn, lane);
-      __syncwarp();
+      if (RANKS) {
+        // dense ranks: one atomicAdd per warp for the round (lane order
+        // within each q, q after q), so the warp's new ranks are contiguous
+        uint32_t total = 0;
+#pragma unroll
+        for (int q = 0; q < kIdsPerRound; ++q) {
+          const uint32_t m = __ballot_sync(kFull, (newbits >> q) & 1u);
+          prevq[q] = total + __popc(m & lanemask_lt());  // rank offset of this lane's q-th new id
+          total += __popc(m);
+        }
+        uint32_t wbase = 0;
+        if (lane == 0 && total) wbase = atomicAdd(S.ucount, total);
+        wbase = __shfl_sync(kFull, wbase, 0);
+#pragma unroll
+        for (int q = 0; q < kIdsPerRound; ++q)
+          if ((newbits >> q) & 1u) {
+            const uint32_t rk = wbase + prevq[q];
+            if (rk < a.ucap) {
+              S.dense[hq[q]] = (uint16_t)rk;
+              S.uniq[rk] = idq[q];
+            } else {
+              atomicOr(a.err, EBIT_CAPACITY);
+            }
+          }
+#pragma unroll
+        for (int q = 0; q < kIdsPerRound; ++q) {
+          const uint32_t i = rbase + q * NT + tid;
+          if (i < n) S.map[i] = (uint16_t)hq[q];
+        }
+        __syncwarp();
+        consume(wbase, wbase + total, lane);
+        __syncwarp();
+      }
     }
   }
+}
+
+// dedup, shading each new vertex as soon as its warp finds it: on return
+// S.vsh holds every unique vertex shaded.
+template <int DEDUP, int SH, class Sync>
+__device__ __forceinline__ void dedup_and_shade(const DrawArgs& a, const Uniforms& u, const float* palette,
+                                                const BatchSmem& S, const uint32_t* ids, uint32_t n, uint32_t tid,
+                                                uint32_t NT, Sync sync) {
+  dedup<DEDUP, true>(a, S, ids, n, tid, NT, sync, ShadeQueue<SH>{a, u, palette, S.vsh, S.uniq});
 }
 
 // Writes corners [cbase, cbase + nc) of the batch (local corner numbering)

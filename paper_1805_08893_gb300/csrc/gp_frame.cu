@@ -18,7 +18,7 @@
 namespace gp {
 
 struct FrameSlice {
-  uint32_t off_misc, off_win, off_map, off_keys, off_table, off_dense, off_uniq, off_v, off_stage, off_wq, total;
+  uint32_t off_misc, off_win, off_map, off_keys, off_table, off_dense, off_uniq, off_v, off_stage, total;
 };
 
 __host__ __device__ inline uint32_t fr_align(uint32_t x, uint32_t a) { return (x + a - 1) / a * a; }
@@ -42,7 +42,6 @@ __host__ __device__ inline FrameSlice frame_slice(int method, int K, int KS, uin
   L.off_uniq = o; o = fr_align(o + ucap * 4, 16);
   L.off_v = o; o = fr_align(o + ucap * KS * 4, 16);
   L.off_stage = o; o = fr_align(o + (fr_align(max_idx, 3) * K + 4) * 4, 16);
-  L.off_wq = o; o = fr_align(o + group * kIdsPerRound * 2, 16);
   L.total = o;
   return L;
 }
@@ -152,7 +151,6 @@ __device__ __noinline__ uint2 frame_group(const FrameDraw& D, uint32_t item, uns
   S.dense = reinterpret_cast<uint16_t*>(base + L.off_dense);
   S.uniq = reinterpret_cast<uint32_t*>(base + L.off_uniq);
   S.vsh = reinterpret_cast<float*>(base + L.off_v);
-  S.wq = reinterpret_cast<uint16_t*>(base + L.off_wq) + (gt >> 5) * (32 * kIdsPerRound);
   S.ucount = misc;
   S.wsum = misc + 8;
 

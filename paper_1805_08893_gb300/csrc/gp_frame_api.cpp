@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -159,6 +160,8 @@ gp_status frame_create_locked(gp_ctx* c, const gp_draw_desc* draws, uint32_t n, 
   if ((e = cudaMalloc(&f->d_rec, sizeof(DevRec))) != cudaSuccess ||
       (e = cudaMalloc(&f->d_work, 16)) != cudaSuccess)
     return abort(cuda_fail(c, e, "cudaMalloc"));
+  std::map<std::tuple<uintptr_t, uint64_t, uint32_t, uint32_t>, uint32_t> shared_part;
+  std::vector<uint32_t> part_src(n, 0);
 
   for (uint32_t i = 0; i < n; ++i) {
     const gp_draw_desc& d = draws[i];
@@ -208,15 +211,27 @@ gp_status frame_create_locked(gp_ctx* c, const gp_draw_desc* draws, uint32_t n, 
       a.num_batches = D.num_batches;
     } else {
       D.dynamic = 1;
-      Partition& p = f->parts[i];
-      if ((s = size_partition(c, p, d.index_buf.num_indices, false, k.max_unique, k.max_tris,
-                              c->cfg.segment_tris)) != GP_OK)
-        return abort(s);
-      p.idx = d.index_buf.d_indices;
-      if (T && (s = run_partition(c, p, d.index_buf.d_indices, d.index_buf.num_indices, c->stream)) != GP_OK)
-        return abort(s);
-      a.starts = p.d_starts;
-      a.num_batches_dev = p.d_count;
+      // draws over the same index buffer with the same limits share one partition
+      const auto key = std::make_tuple(reinterpret_cast<uintptr_t>(d.index_buf.d_indices), d.index_buf.num_indices,
+                                       k.max_unique, k.max_tris);
+      const auto it = shared_part.find(key);
+      if (it != shared_part.end()) {
+        part_src[i] = it->second;
+        a.starts = f->parts[it->second].d_starts;
+        a.num_batches_dev = f->parts[it->second].d_count;
+      } else {
+        Partition& p = f->parts[i];
+        if ((s = size_partition(c, p, d.index_buf.num_indices, false, k.max_unique, k.max_tris,
+                                c->cfg.segment_tris)) != GP_OK)
+          return abort(s);
+        p.idx = d.index_buf.d_indices;
+        if (T && (s = run_partition(c, p, d.index_buf.d_indices, d.index_buf.num_indices, c->stream)) != GP_OK)
+          return abort(s);
+        a.starts = p.d_starts;
+        a.num_batches_dev = p.d_count;
+        shared_part.emplace(key, i);
+        part_src[i] = i;
+      }
     }
     f->cfg[i] = k;
     f->tris += T;
@@ -233,8 +248,11 @@ gp_status frame_create_locked(gp_ctx* c, const gp_draw_desc* draws, uint32_t n, 
     if (D.dynamic) {
       uint32_t cnt = 0;
       if (D.a.num_tris) {
-        if ((e = cudaMemcpy(&cnt, f->parts[i].d_count, 4, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        if (part_src[i] != i) {
+          cnt = f->h_draws[part_src[i]].num_batches;  // set earlier in this loop (part_src[i] < i)
+        } else if ((e = cudaMemcpy(&cnt, f->parts[i].d_count, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) {
           return abort(cuda_fail(c, e, "partition count"));
+        }
       }
       D.num_batches = cnt;
     }
@@ -371,6 +389,10 @@ gp_status gp_frame_destroy(gp_frame* f) {
 // autotuner
 // ---------------------------------------------------------------------------
 
+// Size of a tuning frame: about this many triangles, in at most this many draws.
+constexpr uint64_t kTuneTris = 1u << 22;
+constexpr uint64_t kTuneMaxDraws = 4096;
+
 gp_status gp_autotune(gp_ctx* c, const gp_draw_desc* samples, uint32_t num_samples, uint32_t reps) {
   if (!c) return GP_ERR_INVALID;
   std::lock_guard<std::mutex> lk(c->mu);
@@ -446,6 +468,18 @@ gp_status gp_autotune(gp_ctx* c, const gp_draw_desc* samples, uint32_t num_sampl
     const size_t mid = ids.size() / 2, lo = mid >= 2 ? mid - 2 : 0;
     std::vector<gp_draw_desc> pick;
     for (size_t j = lo; j < ids.size() && pick.size() < 4; ++j) pick.push_back(samples[ids[j]]);
+    // Candidates are ranked by throughput, the quantity a frame of many draws
+    // sees: the samples are repeated until the tuning frame holds enough
+    // triangles to fill every SM several times over (a handful of small
+    // draws would rank configurations by latency instead).  Repeats of a
+    // draw write the same values to the same output.
+    uint64_t pick_tris = 0;
+    for (const gp_draw_desc& d : pick) pick_tris += d.index_buf.num_indices / 3;
+    const uint64_t copies = std::min<uint64_t>(std::max<uint64_t>(1, (kTuneTris + pick_tris - 1) / pick_tris),
+                                               kTuneMaxDraws / pick.size());
+    const size_t nunique = pick.size();
+    for (uint64_t r = 1; r < copies; ++r)
+      for (size_t j = 0; j < nunique; ++j) pick.push_back(pick[j]);
     double best = 1e30;
     gp_draw_config best_k{};
     for (const gp_draw_config& k0 : cand) {
