@@ -88,15 +88,22 @@ def dram_traffic_record():
         rec = json.load(open(p))
     except Exception:
         return None
-    import hashlib
-    src = os.path.join(ROOT, rec.get("source", ""))
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        h = sources_sha256(rec.get("sources", []))
     except Exception:
         return None
-    if h != rec.get("source_sha256"):
+    if not rec.get("sources") or h != rec.get("sources_sha256"):
         return None
     return rec
+
+
+def sources_sha256(paths):
+    """sha256 over the given repository files, concatenated in order."""
+    import hashlib
+    m = hashlib.sha256()
+    for rel in paths:
+        m.update(open(os.path.join(ROOT, rel), "rb").read())
+    return m.hexdigest()
 
 
 class ClockSampler:

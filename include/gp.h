@@ -101,9 +101,10 @@ typedef struct gp_config {
   uint32_t probe_k;           /* parallel hash: per-thread probes before the warp
                                  cooperates [4]; Section 3.4 */
   uint32_t hash_slots;        /* hash table slots, a power of two >= unique capacity and
-                                 <= 32 x threads_per_group [the larger of the next power
-                                 of two >= 2 x capacity and of min(next power of two >=
-                                 4 x capacity, 1024)] */
+                                 <= 32768 [the larger of the next power of two >= 2 x
+                                 capacity and of min(next power of two >= 4 x capacity,
+                                 1024)]; hash/phash batches hold at most 32 x
+                                 threads_per_group indices */
   uint32_t segment_tris;      /* dynamic partition: also cut at every multiple of this
                                  many triangles [4096]; GP_SEGMENT_NONE = single scan */
   uint32_t flags;             /* reserved, 0 */

@@ -23,9 +23,12 @@ using namespace gp;
 
 namespace {
 thread_local std::string g_create_error;
-// Shared memory a block of the single-draw reuse kernel should stay within,
-// so that four blocks fit on an SM (227 KB each, 1 KB reserved per block).
-constexpr size_t kBatchedSmemTarget = 55 * 1024;
+// Shared memory of an SM and the part the runtime reserves per block; the
+// single-draw reuse kernel sizes its output staging for at most this many
+// resident blocks (its registers allow four blocks of 256 threads).
+constexpr size_t kSmemPerSm = 228 * 1024;
+constexpr size_t kSmemReservedPerBlock = 1024;
+constexpr size_t kMaxBatchedBlocksPerSm = 4;
 }  // namespace
 
 namespace gp {
@@ -397,15 +400,34 @@ gp_status enqueue_draw(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* v
   // collisions, so shorter probe sequences, where the table stays small)
   a.hash_slots = cfg.hash_slots ? cfg.hash_slots : std::max(next_pow2(2 * a.ucap), std::min(next_pow2(4 * a.ucap), 1024u));
   a.hash_slots = std::max(a.hash_slots, next_pow2(threads));
-  if (a.hash_slots > 32u * threads)  // each thread numbers a run of at most 32 slots
-    return fail(c, GP_ERR_UNSUPPORTED, "hash_slots may be at most 32 x threads_per_group");
+  if (dedup != DEDUP_SORT && a.max_batch_idx > 32u * threads)  // a thread numbers at most 32 positions
+    return fail(c, GP_ERR_UNSUPPORTED, "hash/phash batches may hold at most 32 x threads_per_group indices");
+  if (a.hash_slots > 32768u)  // slots are stored in 15 bits
+    return fail(c, GP_ERR_UNSUPPORTED, "hash_slots may be at most 32768");
   a.hash_bits = log2u(a.hash_slots);
   a.sort_n = next_pow2(a.max_batch_idx);
-  // staging for the output: the whole batch while four blocks fit on an SM,
-  // else the largest power-of-two fraction of it that lets them
-  a.out_chunk = (a.max_batch_idx + 2) / 3;
-  while (a.out_chunk > 32 && batched_smem_bytes(dedup, (int)shader, a, (int)threads) > kBatchedSmemTarget)
-    a.out_chunk = (a.out_chunk + 1) / 2;
+  // staging for the output: the largest chunk (the whole batch, or a half,
+  // quarter, ... of it) that keeps the most blocks resident on an SM, up to
+  // four (beyond that the registers limit them)
+  {
+    auto resident = [&](uint32_t chunk) {
+      a.out_chunk = chunk;
+      const size_t need = batched_smem_bytes(dedup, (int)shader, a, (int)threads) + kSmemReservedPerBlock;
+      return std::min<size_t>(kMaxBatchedBlocksPerSm, kSmemPerSm / need);
+    };
+    const uint32_t whole = (a.max_batch_idx + 2) / 3;
+    uint32_t best = whole;
+    size_t best_blocks = resident(whole);
+    for (uint32_t chunk = whole; chunk > 32;) {
+      chunk = (chunk + 1) / 2;
+      const size_t blocks = resident(chunk);
+      if (blocks > best_blocks) {
+        best = chunk;
+        best_blocks = blocks;
+      }
+    }
+    a.out_chunk = best;
+  }
   if (const char* oc = std::getenv("GP_OUT_CHUNK")) {  // tuning override
     const long v = std::strtol(oc, nullptr, 10);
     if (v > 0) a.out_chunk = std::min<uint32_t>((uint32_t)v, (a.max_batch_idx + 2) / 3);

@@ -17,6 +17,7 @@
 
 namespace gp {
 
+constexpr uint32_t kNewFlag = 0x8000u;  // map entry flag (hash/phash without ranks); slots < 2^15
 constexpr int kIdsPerRound = 4;  // indices a thread inserts before its warp takes ranks for the new ones
 
 struct BlockSync {
@@ -239,9 +240,9 @@ __device__ __forceinline__ void bitonic_sort(unsigned long long* keys, uint32_t 
 // rank is S.dense[slot]).  The hash table must be empty on entry; it is left
 // filled (the caller clears it after the barrier).  *S.ucount must be 0 on
 // entry for hash/phash.
-// RANKS == false (hash/phash only): the table and S.map (slots) are all it
-// produces -- no ranks, no uniq, no consume; the caller numbers the filled
-// slots itself (compact_table in the single-draw kernel).
+// RANKS == false (hash/phash only): the table and S.map (slot, with kNewFlag
+// at the one position per id whose CAS stored it) are all it produces -- no
+// ranks, no uniq, no consume; the caller numbers the vertices itself.
 template <int DEDUP, bool RANKS, class Sync, class Consume>
 __device__ __forceinline__ void dedup(const DrawArgs& a, const BatchSmem& S, const uint32_t* ids, uint32_t n,
                                       uint32_t tid, uint32_t NT, Sync sync, const Consume& consume) {
@@ -375,7 +376,9 @@ __device__ __forceinline__ void dedup(const DrawArgs& a, const BatchSmem& S, con
             left &= left - 1;
           }
         }
-        if (active && !RANKS) S.map[i] = (uint16_t)h;
+        // without ranks, bit 15 marks the position whose CAS stored the id
+        // (the caller numbers the vertices in the order of these positions)
+        if (active && !RANKS) S.map[i] = (uint16_t)(h | (is_new ? kNewFlag : 0u));
         idq[q] = id;
         hq[q] = h;
         newbits |= is_new ? (1u << q) : 0u;

@@ -19,10 +19,11 @@
 //      then waits for the rows of b_k, whose copies started one iteration
 //      earlier;
 //   C. shades each unique vertex of b_k once, from its raw row, into the
-//      shaded buffer; then (hash/phash) numbers the filled slots of the table
-//      with a block scan (slot -> dense rank, rank -> id) and clears it, and
-//      starts cp.async copies of b_{k+1}'s rows into the raw buffer, which
-//      the shading has just released;
+//      shaded buffer; then (hash/phash) numbers b_{k+1}'s vertices in the
+//      order of the positions whose CAS stored them (a block scan: slot ->
+//      dense rank, rank -> id), clears the table, and starts cp.async copies
+//      of b_{k+1}'s rows into the raw buffer, which the shading has just
+//      released;
 //   D. assembles b_k's triangles in input order into a staging buffer (each
 //      corner's shaded row, found through the map, then slot -> rank for
 //      hash/phash) and writes it with one bulk (TMA) store per chunk -- by
@@ -83,7 +84,7 @@ struct CornerRank {
   uint32_t U;
   __device__ __forceinline__ uint32_t operator()(uint32_t lc) const {
     uint32_t r = map[lc];
-    if (DEDUP != DEDUP_SORT) r = dense[r];
+    if (DEDUP != DEDUP_SORT) r = dense[r & ~kNewFlag];
     return r < U ? r : 0u;
   }
 };
@@ -215,25 +216,19 @@ __global__ void __launch_bounds__(512, 2) batched_kernel(const __grid_constant__
     __syncthreads();     // barrier 2: dedup done; the current batch's rows are in shared memory
     // --- C: shade the current batch; number the next batch's vertices and
     // start the copies of their rows
-    // hash/phash: each thread owns a contiguous run of spt slots (spt a power
-    // of two <= 32; bit j of 'filled' = slot tid * spt + j holds an id)
-    const uint32_t spt = a.hash_slots / NT;
-    uint32_t* myslots = S.table + tid * spt;
-    uint32_t filled = 0, occ_inc = 0;
+    // hash/phash: the vertices are numbered in the order of the positions
+    // whose CAS stored them, so a run of corners mostly refers to nearby
+    // ranks (fewer bank conflicts when D reads their rows).  Each thread owns
+    // the contiguous positions [p0, p0 + ppt) (ppt <= 32); bit j of 'won' =
+    // position p0 + j stored its id.
+    const uint32_t ppt = (n + NT - 1) / NT, p0 = min(tid * ppt, n), p1 = min(p0 + ppt, n);
+    uint32_t won = 0, occ_inc = 0;
     if (has_next) {
       if (DEDUP == DEDUP_SORT) {
         U_next = min(*S.ucount, a.ucap);
       } else {
-        if (spt == 1) {
-          filled = myslots[0] != kEmpty ? 1u : 0u;
-        } else {
-          for (uint32_t j = 0; j < spt; j += 2) {  // runs of >= 2 slots are 8-byte aligned
-            const uint2 v = *reinterpret_cast<const uint2*>(myslots + j);
-            filled |= (v.x != kEmpty ? 1u : 0u) << j;
-            filled |= (v.y != kEmpty ? 2u : 0u) << j;
-          }
-        }
-        occ_inc = warp_inclusive_scan(__popc(filled));
+        for (uint32_t p = p0; p < p1; ++p) won |= (uint32_t)(nmap[p] >> 15) << (p - p0);
+        occ_inc = warp_inclusive_scan(__popc(won));
         if ((tid & 31) == 31) S.wsum[tid >> 5] = occ_inc;
       }
     }
@@ -268,15 +263,14 @@ __global__ void __launch_bounds__(512, 2) batched_kernel(const __grid_constant__
         const uint32_t wv = lane < nw ? S.wsum[lane] : 0u;
         const uint32_t wi = warp_inclusive_scan(wv);
         const uint32_t total = __shfl_sync(kFull, wi, 31);
-        uint32_t r = __shfl_sync(kFull, wi - wv, tid >> 5) + occ_inc - __popc(filled);
+        uint32_t r = __shfl_sync(kFull, wi - wv, tid >> 5) + occ_inc - __popc(won);
         uint16_t* ndense = densebuf + nbuf * a.hash_slots;
-        uint16_t* mydense = ndense + tid * spt;
-        for (uint32_t f = filled; f; f &= f - 1, ++r) {
-          const uint32_t j = __ffs(f) - 1;
-          const uint32_t id = myslots[j];
-          myslots[j] = kEmpty;  // the table is done: clear it for the batch after
+        for (uint32_t f = won; f; f &= f - 1, ++r) {
+          const uint32_t sl = nmap[p0 + __ffs(f) - 1] & ~kNewFlag;
+          const uint32_t id = S.table[sl];
+          S.table[sl] = kEmpty;  // the table is done: clear it for the batch after
           if (r < a.ucap) {
-            mydense[j] = (uint16_t)r;
+            ndense[sl] = (uint16_t)r;
             nuniq[r] = id;
             if (id < a.num_verts)
 #pragma unroll
