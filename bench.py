@@ -61,6 +61,7 @@ def parse_args():
 # (name, variant, mode, extra config)
 VARIANTS = [
     ("naive", "naive", "static", {}),
+    ("multi", "multi", "static", {}),
     ("warp_s96", "warp", "static", {"batch_indices": 96}),
     ("sort_static_s768", "sort", "static", {"batch_indices": 768}),
     ("hash_static_s768", "hash", "static", {"batch_indices": 768}),
@@ -298,7 +299,7 @@ def heavy_section(gp, torch, args):
     flops_per_vertex = 2 * (16 * 36 + 8)
     props = torch.cuda.get_device_properties(0)
     res = {}
-    for name, variant, mode, extra in [("naive", "naive", 0, {}), ("warp_s96", "warp", 0, {}),
+    for name, variant, mode, extra in [("naive", "naive", 0, {}), ("multi", "multi", 0, {}), ("warp_s96", "warp", 0, {}),
                                        ("hash_dynamic", "hash", 1, {}), ("phash_dynamic", "phash", 1, {}),
                                        ("sort_dynamic", "sort", 1, {}), ("hash_static_s768", "hash", 0,
                                                                          {"batch_indices": 768})]:

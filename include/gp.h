@@ -59,9 +59,13 @@ typedef enum gp_status {
 /* Vertex-reuse method.  GP_NAIVE: Section 3.3 "statically batched naive";
  * GP_WARP: Algorithm 1; GP_SORT: Algorithm 2; GP_HASH: Algorithm 3;
  * GP_PHASH: Section 3.4 parallel hashing; GP_AUTO: chosen per draw by the
- * context's autotune table. */
+ * context's autotune table (frames only).  GP_MULTI: the non-streaming
+ * multi-kernel comparator of Section 5 (Table 2 "multi"): one kernel shades
+ * every vertex of the vertex buffer once into a context-owned buffer
+ * (32 bytes per vertex, grown on demand), a second assembles the triangles
+ * from it; single draws only, static mode, invocations = num_vertices. */
 typedef enum gp_variant {
-  GP_NAIVE = 0, GP_WARP = 1, GP_SORT = 2, GP_HASH = 3, GP_PHASH = 4, GP_AUTO = 5
+  GP_NAIVE = 0, GP_WARP = 1, GP_SORT = 2, GP_HASH = 3, GP_PHASH = 4, GP_AUTO = 5, GP_MULTI = 6
 } gp_variant;
 
 /* Section 3.3 (static) and Section 3.4 (dynamic).  GP_WARP and GP_NAIVE are
@@ -424,7 +428,8 @@ gp_status gp_partition_noalloc(const uint32_t* d_indices, uint64_t num_indices, 
 uint32_t gp_out_floats(uint32_t shader_id);
 
 /* Batches a draw of num_indices indices will use under the context's static
- * configuration (ceil(num_indices / S)); 0 for dynamic mode. */
+ * configuration (ceil(num_indices / S); GP_MULTI: 1 for a non-empty draw);
+ * 0 for dynamic mode. */
 uint64_t gp_static_batch_count(gp_ctx* ctx, uint64_t num_indices);
 
 /* Human-readable text of the context's last error ("" if none); valid until

@@ -29,13 +29,14 @@ __all__ = [
 # enums (gp.h)
 GP_OK, GP_ERR_INVALID, GP_ERR_OOM, GP_ERR_CUDA, GP_ERR_TIMEOUT, GP_ERR_BUSY, GP_ERR_INDEX_RANGE, \
     GP_ERR_UNSUPPORTED = range(8)
-GP_NAIVE, GP_WARP, GP_SORT, GP_HASH, GP_PHASH, GP_AUTO = range(6)
+GP_NAIVE, GP_WARP, GP_SORT, GP_HASH, GP_PHASH, GP_AUTO, GP_MULTI = range(7)
 GP_BATCH_STATIC, GP_BATCH_DYNAMIC = 0, 1
 GP_SHADER_MVP, GP_SHADER_SKIN, GP_SHADER_ENVELOPE, GP_SHADER_LOAD = range(4)
 GP_VFMT_PNU32, GP_VFMT_SKIN64 = 0, 1
 GP_SEGMENT_NONE = 0xFFFFFFFF
 
-VARIANTS = {"naive": GP_NAIVE, "warp": GP_WARP, "sort": GP_SORT, "hash": GP_HASH, "phash": GP_PHASH}
+VARIANTS = {"naive": GP_NAIVE, "warp": GP_WARP, "sort": GP_SORT, "hash": GP_HASH, "phash": GP_PHASH,
+            "multi": GP_MULTI}
 
 
 class gp_config(ctypes.Structure):

@@ -193,7 +193,8 @@ uint32_t default_batch(const gp_config& cfg) {
   if (cfg.batch_indices) return cfg.batch_indices;
   switch (cfg.variant) {
     case GP_WARP: return 96;
-    case GP_NAIVE: return 3 * (cfg.threads_per_group ? cfg.threads_per_group : 256);
+    case GP_NAIVE:
+    case GP_MULTI: return 3 * (cfg.threads_per_group ? cfg.threads_per_group : 256);
     default: return 768;
   }
 }
@@ -345,6 +346,21 @@ gp_status enqueue_draw(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* v
     t.host_inv = 3ull * T;
     t.host_batches = (T + block - 1) / block;
     GP_CUDA(c, launch_naive(a, u, (int)shader, block, c->stream));
+    return GP_OK;
+  }
+  if (cfg.variant == GP_MULTI) {
+    const uint64_t V = vb->num_vertices;
+    if (V > c->shaded_cap) {  // grow the shaded-row buffer (cudaFree waits for draws still using it)
+      if (c->d_shaded) cudaFree(c->d_shaded);
+      c->d_shaded = nullptr;
+      c->shaded_cap = 0;
+      cudaError_t e = cudaMalloc(&c->d_shaded, V * 2 * sizeof(float4));
+      if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc (shaded vertex rows)");
+      c->shaded_cap = V;
+    }
+    t.host_inv = V;  // every vertex of the buffer is shaded once, referenced or not
+    t.host_batches = 1;
+    GP_CUDA(c, launch_multi(a, u, (int)shader, c->d_shaded, (int)threads, c->stream));
     return GP_OK;
   }
   if (cfg.variant == GP_WARP) {
@@ -548,9 +564,9 @@ gp_status gp_create(const gp_config* cfg_in, gp_ctx** out) {
   *out = nullptr;
   if (!cfg_in) return fail(nullptr, GP_ERR_INVALID, "cfg is NULL");
   gp_config cfg = *cfg_in;
-  if (cfg.variant < GP_NAIVE || cfg.variant > GP_PHASH)
+  if ((cfg.variant < GP_NAIVE || cfg.variant > GP_PHASH) && cfg.variant != GP_MULTI)
     return fail(nullptr, cfg.variant == GP_AUTO ? GP_ERR_UNSUPPORTED : GP_ERR_INVALID,
-                "variant must be GP_NAIVE..GP_PHASH for a single-draw context");
+                "variant must be GP_NAIVE..GP_PHASH or GP_MULTI for a single-draw context");
   if (cfg.mode != GP_BATCH_STATIC && cfg.mode != GP_BATCH_DYNAMIC) return fail(nullptr, GP_ERR_INVALID, "bad mode");
   if (!cfg.max_unique) cfg.max_unique = 256;
   if (!cfg.max_tris) cfg.max_tris = 341;
@@ -560,17 +576,17 @@ gp_status gp_create(const gp_config* cfg_in, gp_ctx** out) {
   cfg.batch_indices = default_batch(cfg);
   const uint32_t th = cfg.threads_per_group;
   if (th % 32 || th == 0) return fail(nullptr, GP_ERR_INVALID, "threads_per_group must be a multiple of 32");
-  if (cfg.variant == GP_NAIVE || cfg.variant == GP_WARP) {
-    if (th > 256) return fail(nullptr, GP_ERR_INVALID, "naive/warp blocks are at most 256 threads");
+  if (cfg.variant == GP_NAIVE || cfg.variant == GP_WARP || cfg.variant == GP_MULTI) {
+    if (th > 256) return fail(nullptr, GP_ERR_INVALID, "naive/warp/multi blocks are at most 256 threads");
   } else if ((th & (th - 1)) || th > 512) {
     return fail(nullptr, GP_ERR_INVALID, "sort/hash/phash threads_per_group must be a power of two <= 512");
   }
   if (cfg.batch_indices % 3) return fail(nullptr, GP_ERR_INVALID, "batch_indices must be a multiple of 3");
-  if (cfg.mode == GP_BATCH_DYNAMIC && (cfg.variant == GP_NAIVE || cfg.variant == GP_WARP))
-    return fail(nullptr, GP_ERR_INVALID, "naive and warp voting use static batches");
+  if (cfg.mode == GP_BATCH_DYNAMIC && (cfg.variant == GP_NAIVE || cfg.variant == GP_WARP || cfg.variant == GP_MULTI))
+    return fail(nullptr, GP_ERR_INVALID, "naive, warp voting and multi-kernel use static batches");
   if (cfg.variant == GP_WARP && cfg.batch_indices > 384)
     return fail(nullptr, GP_ERR_INVALID, "warp voting batches are at most 384 indices");
-  if (cfg.variant >= GP_SORT && cfg.mode == GP_BATCH_STATIC && cfg.batch_indices > 4095)
+  if (cfg.variant >= GP_SORT && cfg.variant <= GP_PHASH && cfg.mode == GP_BATCH_STATIC && cfg.batch_indices > 4095)
     return fail(nullptr, GP_ERR_INVALID, "static batches are at most 4095 indices");
   if (cfg.max_unique < 3 || cfg.max_unique > 4096) return fail(nullptr, GP_ERR_INVALID, "max_unique must be in 3..4096");
   if (cfg.max_tris < 1 || cfg.max_tris > 1365) return fail(nullptr, GP_ERR_INVALID, "max_tris must be in 1..1365");
@@ -622,6 +638,7 @@ gp_status gp_destroy(gp_ctx* c) {
     if (c->h_idx) cudaFree(c->h_idx);
     if (c->h_vtx) cudaFree(c->h_vtx);
     if (c->h_out) cudaFree(c->h_out);
+    if (c->d_shaded) cudaFree(c->d_shaded);
     if (c->aux) cudaStreamDestroy(c->aux);
   }
   delete c;
@@ -785,6 +802,7 @@ uint32_t gp_out_floats(uint32_t shader_id) { return shader_id <= GP_SHADER_LOAD 
 
 uint64_t gp_static_batch_count(gp_ctx* c, uint64_t num_indices) {
   if (!c || c->cfg.mode != GP_BATCH_STATIC) return 0;
+  if (c->cfg.variant == GP_MULTI) return num_indices ? 1 : 0;  // the whole draw
   const uint64_t S = c->cfg.batch_indices;
   return (num_indices + S - 1) / S;
 }

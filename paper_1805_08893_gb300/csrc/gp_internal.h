@@ -91,6 +91,10 @@ enum Dedup : int { DEDUP_SORT = 0, DEDUP_HASH = 1, DEDUP_PHASH = 2 };
 
 // Launchers (return the launch error).  'shader' is a gp_shader_id.
 cudaError_t launch_naive(const DrawArgs& a, const Uniforms& u, int shader, int block, cudaStream_t s);
+// Multi-kernel comparator: shade all num_verts vertices into rows (2 float4
+// per vertex, caller-owned), then assemble the triangles from them.
+cudaError_t launch_multi(const DrawArgs& a, const Uniforms& u, int shader, float4* rows, int block,
+                         cudaStream_t s);
 cudaError_t launch_warp(const DrawArgs& a, const Uniforms& u, int shader, int warps_per_block,
                         int grid, cudaStream_t s);
 int warp_kernel_blocks_per_sm(int shader, int warps_per_block);

@@ -82,6 +82,9 @@ def draw_gpu(mesh, variant, shader_id=S.SHADER_MVP, mode="static", uniforms=None
             st = torch.zeros(nb + 1, dtype=torch.int32, device=device)
             gp.gp_partition_starts(ctx, handle, st)
             r.starts = st.cpu().numpy().astype(np.int64)
+        elif variant == "multi":
+            nb = 1 if T else 0
+            r.starts = np.array([0, T] if T else [0], dtype=np.int64)
         elif variant == "naive":
             per = cfg.get("threads_per_group") or 256
             nb = (T + per - 1) // per
