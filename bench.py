@@ -51,8 +51,8 @@ def parse_args():
     ap.add_argument("--frequency", type=int, default=FREQ, help="geodesic frequency (600 = the benchmark mesh)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--sections", default="heavy,frame,serving",
-                    help="extra workloads after the headline: heavy, frame, serving (comma list, or 'none')")
+    ap.add_argument("--sections", default="heavy,frame,serving,table1,walk",
+                    help="extra workloads after the headline: heavy, frame, serving, table1, walk (comma list, or 'none')")
     ap.add_argument("--clock-warm", type=float, default=1.0,
                     help="seconds of headline draws before its warm-up, so the clock sampler sees the GPU under load")
     return ap.parse_args()
@@ -439,6 +439,75 @@ def frame_section(gp, torch, args):
             "speedup_vs_separate": (ms_sep / out["autotuned"]["ms_per_frame"]) if isinstance(ms_sep, float) else None}
 
 
+def table1_section(gp, torch, args):
+    """Table 1's columns (Section 5.1) on synthetic meshes the size of the
+    paper's sphere, buddha and dragon rows: ideal reuse, the parallel
+    per-multiprocessor LRU cache at 16/32/64 KB (28 multiprocessors, 1024
+    concurrent invocations; host simulator of the library), and the reuse
+    the GPU kernels achieve with warp voting (S = 96) and dynamic batches
+    (256 unique, 1023 indices)."""
+    rows = {}
+    for label, f in (("sphere-sized f=64", 64), ("buddha-sized f=233", 233), ("dragon-sized f=600", 600)):
+        mesh = mg.geodesic_sphere(f, 2)
+        n = len(mesh.indices)
+        row = {"vertices": mesh.num_vertices, "triangles": mesh.num_tris,
+               "ideal": 1.0 - len(np.unique(mesh.indices)) / n}
+        t0 = time.time()
+        for kb in (16, 32, 64):
+            hits = gp.gp_simulate_parallel_cache(mesh.indices, 28, 1024, kb * 1024 // 32)
+            row[f"cache_{kb}kb"] = hits / n
+        row["cache_sim_indices_per_s"] = 3 * n / (time.time() - t0)
+        idx = torch.from_numpy(mesh.indices.view(np.int32)).cuda()
+        verts = torch.from_numpy(mesh.vertices).cuda()
+        out = torch.empty(mesh.num_tris * 21, dtype=torch.float32, device="cuda")
+        M, N = mg.mvp_uniforms(CAM_SEED)
+        uni = gp.uniforms_mvp(M, N)
+        for col, variant, mode, extra in (("warp", "warp", 0, {"batch_indices": 96}), ("dyn", "hash", 1, {})):
+            ctx = gp.gp_create(variant, mode=mode, **extra)
+            h = gp.gp_partition(ctx, idx)[0] if mode else 0
+            gp.gp_submit_drawcall(ctx, idx, verts, gp.GP_SHADER_MVP, uni, out, partition=h)
+            gp.gp_sync(ctx)
+            row[col] = 1.0 - gp.gp_stats(ctx)["invocations"] / n
+            gp.gp_destroy(ctx)
+        rows[label] = row
+        del idx, verts, out
+    return {"workload": "Table 1 columns on synthetic geodesic spheres (Morton order, permuted vertex ids)",
+            "host_threads": os.cpu_count(), "rows": rows}
+
+
+def walk_section(gp, torch, args):
+    """The parallel random walk of Section 5.4: 256 x 256 torus, 300,000
+    agents, 10 steps; per-step time (CUDA events) and cell evaluations per
+    step for every method (warp: 576 agents per block; sort/hash/phash:
+    static batches of 512 agents, one thread each)."""
+    act = torch.from_numpy(mg.walk_activity(1).view(np.int32)).cuda()
+    keys0 = torch.from_numpy(mg.walk_agents(1).view(np.int32)).cuda()
+    res = {}
+    for variant, batch, threads in (("naive", 256, 0), ("warp", 576, 0), ("sort", 512, 512), ("hash", 512, 512),
+                                    ("phash", 512, 512)):
+        pos = keys0.clone()
+        scratch = torch.empty_like(pos)
+        cnt = torch.zeros(3, dtype=torch.int64, device="cuda")
+        gp.gp_random_walk(act, pos, scratch, cnt, 10, 7, variant, batch_agents=batch, threads=threads)  # warm-up
+        times = []
+        for rep in range(3):
+            pos.copy_(keys0)
+            cnt.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            gp.gp_random_walk(act, pos, scratch, cnt, 10, 7, variant, batch_agents=batch, threads=threads)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        res[variant] = {"ms_per_step": min(times) / 10, "evaluations_per_step": int(cnt[0].item()) / 10,
+                        "batch_agents": batch, "threads": threads or 256}
+    naive = res["naive"]["ms_per_step"]
+    for v in res.values():
+        v["vs_naive"] = naive / v["ms_per_step"]
+    return {"workload": "random walk, 256x256 torus, 300000 agents, 10 steps, 8 Gaussians, moves up to 16 cells",
+            "methods": res}
+
+
 def serving_section(gp, torch, args):
     """Serving: Poisson arrivals, sizes log-uniform in [50, 200,000]
     triangles from a pool of resident meshes (MVP and skinning shaders),
@@ -694,7 +763,8 @@ def main():
             del idx, verts, out
             torch.cuda.empty_cache()
             extra = {}
-            for name, fn in (("heavy", heavy_section), ("frame", frame_section), ("serving", serving_section)):
+            for name, fn in (("heavy", heavy_section), ("frame", frame_section), ("serving", serving_section),
+                             ("table1", table1_section), ("walk", walk_section)):
                 if name in sections:
                     t0 = time.time()
                     try:

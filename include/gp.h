@@ -424,6 +424,71 @@ gp_status gp_partition_noalloc(const uint32_t* d_indices, uint64_t num_indices, 
                                uint32_t max_tris, uint32_t segment_tris, uint32_t* d_starts,
                                uint64_t starts_capacity, uint32_t* d_num_batches, void* stream);
 
+/* ---------------------------------------------------------------------
+ * Cache comparator (host only, no GPU needed)
+ * ------------------------------------------------------------------- */
+
+/* The per-multiprocessor LRU vertex cache the paper compares batching with
+ * (Section 5.1, Table 1 "Parallel Cache"; 28 multiprocessors, 1024
+ * concurrent invocations, 16/32/64 KB in the paper).
+ *
+ * indices:          HOST pointer to num_indices vertex ids (the index
+ *                   buffer); read only.
+ * num_sms:          simulated multiprocessors; the buffer is split into
+ *                   num_sms contiguous parts of ceil(num_indices / num_sms)
+ *                   indices, each worked through in shading cycles of
+ *                   `concurrent` consecutive indices.
+ * concurrent:       invocations a multiprocessor runs at once.  A duplicate
+ *                   index hits only if its vertex was shaded in an EARLIER
+ *                   cycle of the same multiprocessor; the ids that miss are
+ *                   inserted when their cycle ends, in index order.
+ * capacity_entries: cached vertices per multiprocessor (cache bytes / bytes
+ *                   per shaded vertex), <= 2^30.
+ * threads:          host threads simulating multiprocessors side by side
+ *                   (0 = all hardware threads).
+ * *hits:            indices served from a cache; reuse = hits / num_indices.
+ * Returns GP_ERR_INVALID for a NULL pointer or a zero count. */
+gp_status gp_simulate_parallel_cache(const uint32_t* indices, uint64_t num_indices, uint32_t num_sms,
+                                     uint32_t concurrent, uint32_t capacity_entries, uint32_t threads,
+                                     uint64_t* hits);
+
+/* ---------------------------------------------------------------------
+ * Parallel random walk with reuse (Section 5.4)
+ * ------------------------------------------------------------------- */
+
+/* Agents on a toroidal width x height grid, each the packed key
+ * (x << 16) | y.  Per step every agent evaluates the moves (dx, dy) with
+ * 1 <= dx^2 + dy^2 <= 16^2 -- likelihood activity[target] * (65536 / r^2),
+ * exact integers -- keeps the 8 largest (on equal likelihoods the earlier
+ * move in (dy, dx) row-major order from (-16, -16)), and takes one with
+ * probability proportional to its likelihood: u = splitmix64(seed ^
+ * ((step << 32) | agent)), the first kept move whose running sum exceeds
+ * u mod total (no move if the total is 0).  The kept moves depend only on
+ * the cell, so the key is the reuse methods' "index": naive evaluates per
+ * agent, warp per unique key of each 32 agents, sort/hash/phash per unique
+ * key of each static batch of batch_agents agents. */
+typedef struct gp_walk_desc {
+  const uint32_t* d_activity;       /* device [height][width] activity, caller-owned */
+  uint32_t* d_pos;                  /* device [num_agents] keys; in: positions, out: after `steps` steps */
+  uint32_t* d_scratch;              /* device [num_agents], caller-owned scratch */
+  unsigned long long* d_counters;   /* device [3]: += cell evaluations, += batches, |= error bits */
+  void* stream;                     /* cudaStream_t (NULL = default stream) */
+  uint64_t seed;
+  uint32_t width, height;           /* 17..32768 */
+  uint32_t num_agents;
+  int32_t variant;                  /* GP_NAIVE, GP_WARP, GP_SORT, GP_HASH or GP_PHASH */
+  uint32_t first_step;              /* step number of the first step (the random numbers use it) */
+  uint32_t steps;
+  uint32_t batch_agents;            /* agents per batch, a multiple of 32 [576]; <= 1024 for sort/hash/phash */
+  uint32_t threads;                 /* sort/hash/phash: threads per block, a power of two <= 512 [256] */
+} gp_walk_desc;
+
+/* Enqueues `steps` steps on the stream (asynchronous; the counters and
+ * d_pos are final when the stream reaches this point).  Returns
+ * GP_ERR_INVALID for bad sizes, pointers or variants, GP_ERR_CUDA if a launch
+ * fails. */
+gp_status gp_random_walk(const gp_walk_desc* desc);
+
 /* Floats per output corner for a shader (7 or 8), 0 for an unknown id. */
 uint32_t gp_out_floats(uint32_t shader_id);
 

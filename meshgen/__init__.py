@@ -460,3 +460,39 @@ def random_vertices(seed: int, num_vertices: int) -> np.ndarray:
     v[:, 3:6] = n / np.linalg.norm(n, axis=1, keepdims=True)
     v[:, 6:8] = rng.uniform(0, 1, size=(num_vertices, 2))
     return v.astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# random-walk inputs (the parallel random walk of Section 5.4)
+# ---------------------------------------------------------------------------
+
+def walk_activity(seed: int, width: int = 256, height: int = 256, gaussians: int = 8,
+                  scale: int = 4096) -> np.ndarray:
+    """Activity field of the random walk: a floor plus several Gaussians
+    overlaid on a toroidal width x height grid, quantised to integers
+    (uint32 [height, width], values in [scale/20, ~scale * (1/20 + sum of
+    amplitudes)]).  Centres, widths (8..40 cells) and amplitudes (0.5..1.5)
+    are seeded."""
+    rng = np.random.default_rng(90_000 + seed)
+    cx = rng.uniform(0, width, size=gaussians)
+    cy = rng.uniform(0, height, size=gaussians)
+    sig = rng.uniform(8.0, 40.0, size=gaussians)
+    amp = rng.uniform(0.5, 1.5, size=gaussians)
+    x = np.arange(width, dtype=np.float64)[None, :]
+    y = np.arange(height, dtype=np.float64)[:, None]
+    a = np.full((height, width), 0.05)
+    for g in range(gaussians):
+        dx = np.abs(x - cx[g])
+        dx = np.minimum(dx, width - dx)
+        dy = np.abs(y - cy[g])
+        dy = np.minimum(dy, height - dy)
+        a += amp[g] * np.exp(-(dx * dx + dy * dy) / (2.0 * sig[g] * sig[g]))
+    return np.rint(a * scale).astype(np.uint32)
+
+
+def walk_agents(seed: int, count: int = 300_000, width: int = 256, height: int = 256) -> np.ndarray:
+    """Agents placed uniformly at random; each is the packed key (x << 16) | y."""
+    rng = np.random.default_rng(91_000 + seed)
+    x = rng.integers(0, width, size=count, dtype=np.uint64)
+    y = rng.integers(0, height, size=count, dtype=np.uint64)
+    return ((x << np.uint64(16)) | y).astype(np.uint32)

@@ -17,9 +17,11 @@ Software Geometry Processing"):
   not fix: static and dynamic batch boundaries (Sections 3.3, 3.4), and the
   shading-invocation counts of warp voting (Algorithm 1), sorting
   (Algorithm 2) and hashing (Algorithm 3), replayed step by step.
+* ``cache_sim`` -- the simulated per-multiprocessor LRU vertex cache the paper
+  compares batching against (Section 5.1, Table 1).
 
 Every function's docstring cites the passage it follows.  Pins (closed forms,
 hand-worked cases, brute force, the paper's printed numbers) live in
 ``tests/test_oracle_*.py`` and ``tests/golden/``.
 """
-from . import batching, shading  # noqa: F401
+from . import batching, cache_sim, shading  # noqa: F401

@@ -120,6 +120,14 @@ class gp_serve_stats(ctypes.Structure):
                 ("wall_ms", ctypes.c_double), ("last_error", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
 
 
+class gp_walk_desc(ctypes.Structure):
+    _fields_ = [("d_activity", ctypes.c_void_p), ("d_pos", ctypes.c_void_p), ("d_scratch", ctypes.c_void_p),
+                ("d_counters", ctypes.c_void_p), ("stream", ctypes.c_void_p), ("seed", ctypes.c_uint64),
+                ("width", ctypes.c_uint32), ("height", ctypes.c_uint32), ("num_agents", ctypes.c_uint32),
+                ("variant", ctypes.c_int32), ("first_step", ctypes.c_uint32), ("steps", ctypes.c_uint32),
+                ("batch_agents", ctypes.c_uint32), ("threads", ctypes.c_uint32)]
+
+
 class GpError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(message)
@@ -173,6 +181,8 @@ def _load():
         "gp_server_latency": ([P, U64, ctypes.POINTER(ctypes.c_double)], I),
         "gp_server_stats": ([P, ctypes.POINTER(gp_serve_stats), I], I),
         "gp_server_destroy": ([P], I),
+        "gp_simulate_parallel_cache": ([ctypes.POINTER(U32), U64, U32, U32, U32, U32, ctypes.POINTER(U64)], I),
+        "gp_random_walk": ([ctypes.POINTER(gp_walk_desc)], I),
     }
     for name, (argt, rest) in sig.items():
         f = getattr(L, name)
@@ -488,6 +498,31 @@ def gp_server_stats(server, reset=False) -> dict:
 
 def gp_server_destroy(server):
     _check(lib.gp_server_destroy(server))
+
+
+def gp_simulate_parallel_cache(indices, num_sms=28, concurrent=1024, capacity_entries=512, threads=0) -> int:
+    """gp_simulate_parallel_cache: hits of the per-multiprocessor LRU cache
+    (Section 5.1).  ``indices``: host uint32 array (numpy)."""
+    a = np.ascontiguousarray(indices, dtype=np.uint32)
+    hits = ctypes.c_uint64()
+    _check(lib.gp_simulate_parallel_cache(a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), a.size, num_sms,
+                                          concurrent, capacity_entries, threads, ctypes.byref(hits)))
+    return hits.value
+
+
+def gp_random_walk(activity, pos, scratch, counters, steps, seed, variant="hash", first_step=0, batch_agents=0,
+                   threads=0, stream=None):
+    """gp_random_walk: ``activity`` uint32/int32 CUDA tensor [height, width];
+    ``pos``/``scratch`` uint32/int32 CUDA tensors [num_agents] (pos is updated
+    in place); ``counters`` int64 CUDA tensor [3] (accumulated)."""
+    for t in (activity, pos, scratch, counters):
+        assert t.is_cuda and t.is_contiguous()
+    assert activity.element_size() == 4 and pos.element_size() == 4 and counters.element_size() == 8
+    h, w = activity.shape
+    d = gp_walk_desc(activity.data_ptr(), pos.data_ptr(), scratch.data_ptr(), counters.data_ptr(),
+                     _stream_handle(stream), seed, w, h, pos.numel(), VARIANTS.get(variant, variant), first_step,
+                     steps, batch_agents, threads)
+    _check(lib.gp_random_walk(ctypes.byref(d)))
 
 
 def gp_out_floats(shader_id: int) -> int:
