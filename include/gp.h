@@ -223,8 +223,14 @@ gp_status gp_stats(gp_ctx* ctx, gp_stats_t* out, int reset);
 
 /* End-to-end draw from HOST memory: copies the indices and vertices to
  * context-owned device buffers, partitions (dynamic mode), draws, copies the
- * output back to out_host (capacity in bytes) and waits.  Pinned host memory
- * gives full copy bandwidth; pageable memory works but is slower. */
+ * output back to out_host (capacity in bytes) and waits.  The triangles go in
+ * chunks of about 2^20, each a whole number of batches (segments for dynamic
+ * mode, static batches, naive blocks), so the batches and the output are
+ * those of one draw; each chunk's upload, draw and read-back overlap those of
+ * its neighbours on separate streams, and each chunk counts as one draw in
+ * gp_stats.  GP_MULTI and the unsegmented partition run as one chunk.
+ * Pinned host memory gives full copy bandwidth; pageable memory works but is
+ * slower. */
 gp_status gp_draw_host(gp_ctx* ctx, const uint32_t* indices_host, uint64_t num_indices,
                        const void* vertices_host, uint64_t num_vertices, uint32_t stride_bytes,
                        uint32_t format, uint32_t shader_id, const void* uniforms, uint32_t uniforms_bytes,

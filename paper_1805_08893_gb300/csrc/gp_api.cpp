@@ -29,6 +29,11 @@ thread_local std::string g_create_error;
 constexpr size_t kSmemPerSm = 228 * 1024;
 constexpr size_t kSmemReservedPerBlock = 1024;
 constexpr size_t kMaxBatchedBlocksPerSm = 4;
+// gp_draw_host: triangles per chunk (rounded to whole batches); uploads,
+// draws and read-backs of consecutive chunks overlap.  The host link bounds
+// this path; smaller chunks start the read-back earlier but add per-chunk
+// partition and launch work (2^18 measured slower than 2^20).
+constexpr uint64_t kHostChunkTris = 1u << 20;
 }  // namespace
 
 namespace gp {
@@ -639,6 +644,8 @@ gp_status gp_destroy(gp_ctx* c) {
     if (c->h_vtx) cudaFree(c->h_vtx);
     if (c->h_out) cudaFree(c->h_out);
     if (c->d_shaded) cudaFree(c->d_shaded);
+    if (c->copy_in) cudaStreamDestroy(c->copy_in);
+    if (c->copy_out) cudaStreamDestroy(c->copy_out);
     if (c->aux) cudaStreamDestroy(c->aux);
   }
   delete c;
@@ -777,24 +784,73 @@ gp_status gp_draw_host(gp_ctx* c, const uint32_t* indices_host, uint64_t num_ind
   if ((num_indices && !indices_host) || (num_vertices && !vertices_host) || (num_indices && !out_host))
     return fail(c, GP_ERR_INVALID, "NULL host buffer");
   if (shader_id > GP_SHADER_LOAD) return fail(c, GP_ERR_INVALID, "unknown shader_id");
+  if (num_indices % 3) return fail(c, GP_ERR_INVALID, "num_indices is not a multiple of 3");
   const uint64_t T = num_indices / 3;
-  const size_t out_bytes = (size_t)T * 3 * out_floats((int)shader_id) * 4;
+  const uint32_t K = (uint32_t)out_floats((int)shader_id);
+  const size_t out_bytes = (size_t)T * 3 * K * 4;
   if (out_capacity_bytes < out_bytes) return fail(c, GP_ERR_INVALID, "out capacity too small");
   gp_status s;
   if ((s = ensure_buf(c, &c->h_idx, &c->h_idx_cap, num_indices * 4)) != GP_OK) return s;
   if ((s = ensure_buf(c, &c->h_vtx, &c->h_vtx_cap, num_vertices * stride_bytes)) != GP_OK) return s;
   if ((s = ensure_buf(c, &c->h_out, &c->h_out_cap, out_bytes)) != GP_OK) return s;
-  if (num_indices) GP_CUDA(c, cudaMemcpyAsync(c->h_idx, indices_host, num_indices * 4, cudaMemcpyHostToDevice, c->stream));
+  if (!c->copy_in) GP_CUDA(c, cudaStreamCreateWithFlags(&c->copy_in, cudaStreamNonBlocking));
+  if (!c->copy_out) GP_CUDA(c, cudaStreamCreateWithFlags(&c->copy_out, cudaStreamNonBlocking));
+
+  // Chunks of whole batches, so that each chunk's batches are exactly those of
+  // the whole draw: multiples of the segment (dynamic), of the static batch
+  // (sort/hash/phash/warp) or of the block (naive).  The multi-kernel
+  // comparator and the unsegmented partition run as one chunk.
+  const gp_config& cfg = c->cfg;
+  uint64_t granule = 0;
+  if (cfg.variant == GP_MULTI) granule = 0;
+  else if (cfg.mode == GP_BATCH_DYNAMIC) granule = cfg.segment_tris == GP_SEGMENT_NONE ? 0 : cfg.segment_tris;
+  else if (cfg.variant == GP_NAIVE) granule = cfg.threads_per_group;
+  else granule = default_batch(cfg) / 3;
+  uint64_t chunk = T;
+  if (granule) chunk = std::max<uint64_t>(1, (kHostChunkTris + granule / 2) / granule) * granule;
+  if (chunk == 0) chunk = 1;
+
+  std::vector<cudaEvent_t> evs;
+  auto new_event = [&]() {
+    cudaEvent_t e = get_event(c);
+    if (e) evs.push_back(e);
+    return e;
+  };
+  auto finish = [&](gp_status st) {
+    cudaStreamSynchronize(c->copy_in);
+    cudaStreamSynchronize(c->stream);
+    cudaStreamSynchronize(c->copy_out);
+    for (cudaEvent_t e : evs) put_event(c, e);
+    return st;
+  };
+  cudaEvent_t ev_v = new_event();
+  if (!ev_v) return finish(fail(c, GP_ERR_CUDA, "cudaEventCreate failed"));
   if (num_vertices)
-    GP_CUDA(c, cudaMemcpyAsync(c->h_vtx, vertices_host, num_vertices * stride_bytes, cudaMemcpyHostToDevice, c->stream));
-  gp_index_buf ib{static_cast<const uint32_t*>(c->h_idx), num_indices, 0};
-  gp_vertex_buf vb{c->h_vtx, num_vertices, stride_bytes, format};
-  gp_out_buf ob{static_cast<float*>(c->h_out), out_bytes, nullptr, nullptr, 0};
+    GP_CUDA(c, cudaMemcpyAsync(c->h_vtx, vertices_host, num_vertices * stride_bytes, cudaMemcpyHostToDevice,
+                               c->copy_in));
+  GP_CUDA(c, cudaEventRecord(ev_v, c->copy_in));
+  GP_CUDA(c, cudaStreamWaitEvent(c->stream, ev_v, 0));
   uint64_t ticket = 0;
-  s = submit_locked(c, &ib, &vb, shader_id, uniforms, uniforms_bytes, &ob, &ticket);
-  if (s != GP_OK) return s;
-  if (out_bytes) GP_CUDA(c, cudaMemcpyAsync(out_host, c->h_out, out_bytes, cudaMemcpyDeviceToHost, c->stream));
-  GP_CUDA(c, cudaStreamSynchronize(c->stream));
+  gp_vertex_buf vb{c->h_vtx, num_vertices, stride_bytes, format};
+  for (uint64_t t0 = 0; t0 < T || (T == 0 && t0 == 0); t0 += chunk) {
+    const uint64_t nt = std::min<uint64_t>(chunk, T - t0);
+    uint32_t* d_idx = static_cast<uint32_t*>(c->h_idx) + 3 * t0;
+    float* d_out = static_cast<float*>(c->h_out) + 3 * K * t0;
+    cudaEvent_t ev_in = new_event(), ev_done = new_event();
+    if (!ev_in || !ev_done) return finish(fail(c, GP_ERR_CUDA, "cudaEventCreate failed"));
+    if (nt) GP_CUDA(c, cudaMemcpyAsync(d_idx, indices_host + 3 * t0, nt * 12, cudaMemcpyHostToDevice, c->copy_in));
+    GP_CUDA(c, cudaEventRecord(ev_in, c->copy_in));
+    GP_CUDA(c, cudaStreamWaitEvent(c->stream, ev_in, 0));
+    gp_index_buf ib{d_idx, 3 * nt, 0};
+    gp_out_buf ob{d_out, nt * 3 * K * 4, nullptr, nullptr, 0};
+    s = submit_locked(c, &ib, &vb, shader_id, uniforms, uniforms_bytes, &ob, &ticket);
+    if (s != GP_OK) return finish(s);
+    GP_CUDA(c, cudaEventRecord(ev_done, c->stream));
+    GP_CUDA(c, cudaStreamWaitEvent(c->copy_out, ev_done, 0));
+    if (nt) GP_CUDA(c, cudaMemcpyAsync(out_host + 3 * K * t0, d_out, nt * 3 * K * 4, cudaMemcpyDeviceToHost, c->copy_out));
+    if (T == 0) break;
+  }
+  s = finish(GP_OK);
   return sync_locked(c, ticket, 0);
 }
 

@@ -80,31 +80,37 @@ __global__ void __launch_bounds__(256) partition_segments_kernel(const __grid_co
     for (uint32_t c = 0; c < wt; c += 32) {
       const uint32_t j = c + lane;
       const bool valid = j < wt;
-      uint32_t slot0 = 0, slot1 = 0, slot2 = 0;
+      // the triangle's three ids: insert them (three independent CAS, then
+      // the rare collisions), record their positions (three independent
+      // atomicMin), and count the ids whose smallest position is here
+      uint32_t x[3], h[3], prev[3];
       if (valid) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          const uint32_t x = win[3 * j + k];
-          uint32_t h = part_hash(x, p.table_bits);
-          for (uint32_t probes = 0;; ++probes) {
-            const uint32_t prev = atomicCAS(&keys[h], kEmpty, x);
-            if (prev == kEmpty || prev == x) break;
-            h = (h + 1) & mask;
+          x[k] = win[3 * j + k];
+          h[k] = part_hash(x[k], p.table_bits);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) prev[k] = atomicCAS(&keys[h[k]], kEmpty, x[k]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          for (uint32_t probes = 0; prev[k] != kEmpty && prev[k] != x[k]; ++probes) {
             if (probes > p.table_slots) {  // cannot happen: the table has room
               atomicOr(p.err, EBIT_CAPACITY);
               break;
             }
+            h[k] = (h[k] + 1) & mask;
+            prev[k] = atomicCAS(&keys[h[k]], kEmpty, x[k]);
           }
-          atomicMin(&pos[h], 3 * j + k);
-          if (k == 0) slot0 = h; else if (k == 1) slot1 = h; else slot2 = h;
         }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) atomicMin(&pos[h[k]], 3 * j + k);
       }
       __syncwarp();
       uint32_t fresh = 0;
       if (valid) {
-        fresh += pos[slot0] == 3 * j + 0;
-        fresh += pos[slot1] == 3 * j + 1;
-        fresh += pos[slot2] == 3 * j + 2;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) fresh += pos[h[k]] == 3 * j + k;
       }
       const uint32_t cum = warp_inclusive_scan(fresh);
       const uint32_t over = __ballot_sync(kFull, valid && nu + cum > p.max_unique);

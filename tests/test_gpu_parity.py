@@ -237,3 +237,33 @@ def test_host_buffer_draw_matches_device_draw(sphere):
             gp.gp_destroy(ctx)
         dev = draw_gpu(sphere, variant, S.SHADER_MVP, "dynamic" if mode else "static", uni, debug=False).out
         assert np.array_equal(got.view(np.uint32), dev.view(np.uint32))
+
+
+@pytest.mark.parametrize("variant,mode,extra", [("hash", 1, {}), ("sort", 0, {"batch_indices": 255}),
+                                                ("naive", 0, {}), ("warp", 0, {}), ("multi", 0, {})])
+def test_host_buffer_draw_in_chunks(variant, mode, extra):
+    # more than 2^20 triangles: the host draw runs in chunks of whole batches,
+    # whose output must equal one device draw bit for bit, and the oracle on
+    # sampled triangles
+    import torch
+    import paper_1805_08893_gb300 as gp
+    mesh = mg.geodesic_sphere(245, 8)  # 1,200,500 triangles
+    uni, uni_o = uniforms_for(mesh, S.SHADER_MVP)
+    ctx = gp.gp_create(variant, mode=mode, **extra)
+    try:
+        out = torch.full((mesh.num_tris * 21,), float("nan"), dtype=torch.float32).pin_memory()
+        idx = torch.from_numpy(mesh.indices.view(np.int32)).pin_memory()
+        verts = torch.from_numpy(mesh.vertices).pin_memory()
+        gp.gp_draw_host(ctx, idx, verts, gp.GP_SHADER_MVP, uni, out)
+        got = out.numpy().reshape(-1, 3, 7)
+        st = gp.gp_stats(ctx)
+        assert st["triangles"] == mesh.num_tris
+        if variant != "multi":
+            assert st["draws"] >= 2  # chunked
+    finally:
+        gp.gp_destroy(ctx)
+    dev = draw_gpu(mesh, variant, S.SHADER_MVP, "dynamic" if mode else "static", uni, debug=False, **extra).out
+    assert np.array_equal(got.view(np.uint32), dev.view(np.uint32))
+    rng = np.random.default_rng(1)
+    tris = np.sort(rng.choice(mesh.num_tris, size=2000, replace=False))
+    assert_attrs_close(got[tris], S.draw(mesh, S.SHADER_MVP, uni_o, tris=tris), S.SHADER_MVP, mesh)
