@@ -51,8 +51,8 @@ def parse_args():
     ap.add_argument("--frequency", type=int, default=FREQ, help="geodesic frequency (600 = the benchmark mesh)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--sections", default="heavy,frame,serving,table1,walk",
-                    help="extra workloads after the headline: heavy, frame, serving, table1, walk (comma list, or 'none')")
+    ap.add_argument("--sections", default="heavy,frame,serving,table1,walk,loop",
+                    help="extra workloads: heavy, frame, serving, table1, walk, loop (comma list, or 'none')")
     ap.add_argument("--clock-warm", type=float, default=1.0,
                     help="seconds of headline draws before its warm-up, so the clock sampler sees the GPU under load")
     return ap.parse_args()
@@ -508,6 +508,54 @@ def walk_section(gp, torch, args):
             "methods": res}
 
 
+def loop_section(gp, torch, args):
+    """One Loop subdivision step (Section 5.2) on synthetic meshes the size of
+    the paper's sphere and buddha: naive, sort (static batches of 768, 256
+    threads) and hash / parallel hash (dynamic batches of up to 192 indices
+    and 64 unique vertices, 64 threads), the paper's best settings; CUDA
+    events, adjacency built once beforehand."""
+    res = {}
+    for label, f in (("sphere-sized f=64", 64), ("buddha-sized f=233", 233)):
+        mesh = mg.geodesic_sphere(f, 2)
+        adj = [torch.from_numpy(x.view(np.int32).copy()).cuda()
+               for x in gp.gp_loop_adjacency(mesh.indices, mesh.num_vertices)]
+        idx = torch.from_numpy(mesh.indices.view(np.int32)).cuda()
+        verts = torch.from_numpy(mesh.vertices).cuda()
+        out = torch.empty(mesh.num_tris * 36, device="cuda")
+        cnt = torch.zeros(3, dtype=torch.int64, device="cuda")
+        ctx = gp.gp_create("hash", mode=gp.GP_BATCH_DYNAMIC, max_unique=64, max_tris=64)
+        h, nb = gp.gp_partition(ctx, idx)
+        starts = torch.zeros(nb + 1, dtype=torch.int32, device="cuda")
+        gp.gp_partition_starts(ctx, h, starts)
+        count = torch.tensor([nb], dtype=torch.int32, device="cuda")
+        row = {"triangles": mesh.num_tris}
+        for name, variant, kw in (("naive", "naive", {}), ("sort_s768", "sort", {"batch_indices": 768}),
+                                  ("hash_dyn192", "hash", {"starts": starts, "num_batches": count, "max_batches": nb,
+                                                           "max_batch_indices": 192, "max_unique": 64,
+                                                           "threads": 64}),
+                                  ("phash_dyn192", "phash", {"starts": starts, "num_batches": count, "max_batches": nb,
+                                                             "max_batch_indices": 192, "max_unique": 64,
+                                                             "threads": 64})):
+            for _ in range(3):
+                gp.gp_loop_subdivide(idx, verts, adj, out, cnt, variant, **kw)
+            cnt.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(10):
+                gp.gp_loop_subdivide(idx, verts, adj, out, cnt, variant, **kw)
+            e1.record()
+            torch.cuda.synchronize()
+            row[name] = {"ms": e0.elapsed_time(e1) / 10, "vertex_rule_evaluations": int(cnt[0].item()) // 10}
+        naive = row["naive"]["ms"]
+        for k, v in row.items():
+            if isinstance(v, dict):
+                v["vs_naive"] = naive / v["ms"]
+        gp.gp_partition_release(ctx, h)
+        gp.gp_destroy(ctx)
+        res[label] = row
+    return {"workload": "one Loop subdivision step, geodesic spheres (closed 2-manifolds)", "meshes": res}
+
+
 def serving_section(gp, torch, args):
     """Serving: Poisson arrivals, sizes log-uniform in [50, 200,000]
     triangles from a pool of resident meshes (MVP and skinning shaders),
@@ -764,7 +812,7 @@ def main():
             torch.cuda.empty_cache()
             extra = {}
             for name, fn in (("heavy", heavy_section), ("frame", frame_section), ("serving", serving_section),
-                             ("table1", table1_section), ("walk", walk_section)):
+                             ("table1", table1_section), ("walk", walk_section), ("loop", loop_section)):
                 if name in sections:
                     t0 = time.time()
                     try:

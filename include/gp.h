@@ -495,6 +495,64 @@ typedef struct gp_walk_desc {
  * fails. */
 gp_status gp_random_walk(const gp_walk_desc* desc);
 
+/* ---------------------------------------------------------------------
+ * Loop subdivision with reuse (Section 5.2)
+ * ------------------------------------------------------------------- */
+
+/* Adjacency for gp_loop_subdivide, built on the host from HOST arrays:
+ *   ring_offsets [num_vertices + 1], ring [ring_capacity]: vertex v's 1-ring
+ *     is ring[ring_offsets[v] .. ring_offsets[v+1]): its distinct neighbours
+ *     in order of first appearance, or -- for a boundary vertex (an edge
+ *     used by one triangle; vertex_flags[v] bit 0 set) -- its two boundary
+ *     neighbours (a vertex with more than two is treated as interior);
+ *   opposite [num_indices]: for edge (v_k, v_k+1) of triangle t, the third
+ *     vertex of the other triangle on that edge, 0xFFFFFFFF on a boundary;
+ *   *ring_count: entries the rings need.  ring may be NULL (or too small:
+ *     GP_ERR_INVALID) to query the size first.
+ * GP_ERR_INDEX_RANGE for an index >= num_vertices. */
+gp_status gp_loop_adjacency(const uint32_t* indices, uint64_t num_indices, uint32_t num_vertices,
+                            uint32_t* ring_offsets, uint32_t* ring, uint64_t ring_capacity, uint32_t* opposite,
+                            uint32_t* vertex_flags, uint64_t* ring_count);
+
+/* One Loop subdivision step, streamed triangle by triangle (Section 5.2, after
+ * Loop's thesis).  Triangle t = (v0, v1, v2) yields output triangles
+ * 4t..4t+3 = (E0, M0, M2), (E1, M1, M0), (E2, M2, M1), (M0, M1, M2):
+ *   E_k = (1 - n beta) v_k + beta * sum of its n ring neighbours, beta =
+ *         (5/8 - (3/8 + cos(2 pi / n) / 4)^2) / n; boundary vertices:
+ *         3/4 v + 1/8 (b0 + b1);
+ *   M_k = 3/8 (v_k + v_k+1) + 1/8 (v_k+2 + opposite vertex); boundary edges:
+ *         the midpoint.
+ * Positions are the first three floats of each vertex row.  The vertex rule
+ * reads a whole ring, so it is what the methods reuse: GP_NAIVE evaluates it
+ * per corner; GP_SORT / GP_HASH / GP_PHASH evaluate it once per unique vertex
+ * of a batch (static batches of batch_indices, or the dynamic batches of a
+ * partition passed in d_starts).  All device buffers are caller-owned; the
+ * call enqueues on `stream` and returns. */
+typedef struct gp_loop_desc {
+  const uint32_t* d_indices;         /* [num_indices], 16-byte aligned */
+  const void* d_vertices;            /* rows of stride_bytes; position = floats 0..2 */
+  const uint32_t* d_ring_offsets;    /* [num_vertices + 1] */
+  const uint32_t* d_ring;            /* [ring_count] */
+  const uint32_t* d_vertex_flags;    /* [num_vertices] */
+  const uint32_t* d_opposite;        /* [num_indices] */
+  float* d_out;                      /* [T][4][3][3], 16-byte aligned */
+  const uint32_t* d_starts;          /* dynamic batch starts (triangles), or NULL for static batches */
+  const uint32_t* d_num_batches;     /* dynamic: device batch count */
+  unsigned long long* d_counters;    /* [3]: += vertex-rule evaluations, += batches, |= error bits */
+  void* stream;                      /* cudaStream_t */
+  uint64_t num_indices, num_vertices, ring_count;
+  uint32_t stride_bytes;             /* >= 12, a multiple of 4 */
+  int32_t variant;                   /* GP_NAIVE, GP_SORT, GP_HASH or GP_PHASH */
+  uint32_t batch_indices;            /* static: indices per batch, a multiple of 3, <= 4095 [768] */
+  uint32_t max_batch_indices;        /* dynamic: 3 x the partition's triangle limit */
+  uint32_t max_unique;               /* dynamic: the partition's unique limit [max_batch_indices] */
+  uint32_t max_batches;              /* dynamic: the number of batches (or more) */
+  uint32_t threads;                  /* sort/hash/phash: threads per block, a power of two <= 512 [256] */
+} gp_loop_desc;
+
+/* GP_ERR_INVALID for bad sizes, pointers, variants or batch limits. */
+gp_status gp_loop_subdivide(const gp_loop_desc* desc);
+
 /* Floats per output corner for a shader (7 or 8), 0 for an unknown id. */
 uint32_t gp_out_floats(uint32_t shader_id);
 

@@ -19,9 +19,11 @@ Software Geometry Processing"):
   (Algorithm 2) and hashing (Algorithm 3), replayed step by step.
 * ``cache_sim`` -- the simulated per-multiprocessor LRU vertex cache the paper
   compares batching against (Section 5.1, Table 1).
+* ``walk`` and ``loop`` -- the applications of Section 5: the parallel random
+  walk (5.4) and Loop subdivision (5.2).
 
 Every function's docstring cites the passage it follows.  Pins (closed forms,
 hand-worked cases, brute force, the paper's printed numbers) live in
 ``tests/test_oracle_*.py`` and ``tests/golden/``.
 """
-from . import batching, cache_sim, shading  # noqa: F401
+from . import batching, cache_sim, loop, shading, walk  # noqa: F401

@@ -128,6 +128,16 @@ class gp_walk_desc(ctypes.Structure):
                 ("batch_agents", ctypes.c_uint32), ("threads", ctypes.c_uint32)]
 
 
+class gp_loop_desc(ctypes.Structure):
+    _fields_ = [("d_indices", ctypes.c_void_p), ("d_vertices", ctypes.c_void_p), ("d_ring_offsets", ctypes.c_void_p),
+                ("d_ring", ctypes.c_void_p), ("d_vertex_flags", ctypes.c_void_p), ("d_opposite", ctypes.c_void_p),
+                ("d_out", ctypes.c_void_p), ("d_starts", ctypes.c_void_p), ("d_num_batches", ctypes.c_void_p),
+                ("d_counters", ctypes.c_void_p), ("stream", ctypes.c_void_p), ("num_indices", ctypes.c_uint64),
+                ("num_vertices", ctypes.c_uint64), ("ring_count", ctypes.c_uint64), ("stride_bytes", ctypes.c_uint32),
+                ("variant", ctypes.c_int32), ("batch_indices", ctypes.c_uint32), ("max_batch_indices", ctypes.c_uint32),
+                ("max_unique", ctypes.c_uint32), ("max_batches", ctypes.c_uint32), ("threads", ctypes.c_uint32)]
+
+
 class GpError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(message)
@@ -183,6 +193,8 @@ def _load():
         "gp_server_destroy": ([P], I),
         "gp_simulate_parallel_cache": ([ctypes.POINTER(U32), U64, U32, U32, U32, U32, ctypes.POINTER(U64)], I),
         "gp_random_walk": ([ctypes.POINTER(gp_walk_desc)], I),
+        "gp_loop_adjacency": ([P, U64, U32, P, P, U64, P, P, ctypes.POINTER(U64)], I),
+        "gp_loop_subdivide": ([ctypes.POINTER(gp_loop_desc)], I),
     }
     for name, (argt, rest) in sig.items():
         f = getattr(L, name)
@@ -523,6 +535,38 @@ def gp_random_walk(activity, pos, scratch, counters, steps, seed, variant="hash"
                      _stream_handle(stream), seed, w, h, pos.numel(), VARIANTS.get(variant, variant), first_step,
                      steps, batch_agents, threads)
     _check(lib.gp_random_walk(ctypes.byref(d)))
+
+
+def gp_loop_adjacency(indices, num_vertices):
+    """gp_loop_adjacency on host arrays: returns (ring_offsets, ring,
+    opposite, vertex_flags) as uint32 numpy arrays."""
+    idx = np.ascontiguousarray(indices, dtype=np.uint32)
+    off = np.zeros(num_vertices + 1, dtype=np.uint32)
+    opp = np.zeros(max(idx.size, 1), dtype=np.uint32)
+    flags = np.zeros(max(num_vertices, 1), dtype=np.uint32)
+    cnt = ctypes.c_uint64()
+    _check(lib.gp_loop_adjacency(idx.ctypes.data, idx.size, num_vertices, off.ctypes.data, None, 0,
+                                 opp.ctypes.data, flags.ctypes.data, ctypes.byref(cnt)))
+    ring = np.zeros(max(cnt.value, 1), dtype=np.uint32)
+    _check(lib.gp_loop_adjacency(idx.ctypes.data, idx.size, num_vertices, off.ctypes.data, ring.ctypes.data,
+                                 ring.size, opp.ctypes.data, flags.ctypes.data, ctypes.byref(cnt)))
+    return off, ring[:cnt.value], opp[:idx.size], flags[:num_vertices]
+
+
+def gp_loop_subdivide(indices, vertices, adjacency, out, counters, variant="hash", batch_indices=0, starts=None,
+                      num_batches=None, max_batches=0, max_batch_indices=0, max_unique=0, threads=0, stream=None):
+    """gp_loop_subdivide: ``adjacency`` = (ring_offsets, ring, opposite,
+    vertex_flags) as CUDA tensors; ``out`` float32 CUDA tensor of T*36
+    floats; ``counters`` int64 CUDA tensor [3]; dynamic batches: ``starts``
+    and ``num_batches`` (CUDA tensors from a partition) with their limits."""
+    off, ring, opp, flags = adjacency
+    d = gp_loop_desc(indices.data_ptr(), vertices.data_ptr(), off.data_ptr(), ring.data_ptr(), flags.data_ptr(),
+                     opp.data_ptr(), out.data_ptr(), None if starts is None else starts.data_ptr(),
+                     None if num_batches is None else num_batches.data_ptr(), counters.data_ptr(),
+                     _stream_handle(stream), indices.numel(), vertices.shape[0], ring.numel(),
+                     vertices.shape[1] * vertices.element_size(), VARIANTS.get(variant, variant), batch_indices,
+                     max_batch_indices, max_unique, max_batches, threads)
+    _check(lib.gp_loop_subdivide(ctypes.byref(d)))
 
 
 def gp_out_floats(shader_id: int) -> int:

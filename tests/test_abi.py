@@ -56,10 +56,10 @@ def test_uniform_struct_sizes_match_header():
     src = r'''
 #include <stdio.h>
 #include "gp.h"
-int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(gp_config), sizeof(gp_index_buf),
+int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(gp_config), sizeof(gp_index_buf),
  sizeof(gp_vertex_buf), sizeof(gp_out_buf), sizeof(gp_uniforms_mvp), sizeof(gp_uniforms_skin),
  sizeof(gp_uniforms_envelope), sizeof(gp_stats_t), sizeof(gp_draw_desc), sizeof(gp_draw_config),
- sizeof(gp_autotune_entry), sizeof(gp_serve_config), sizeof(gp_serve_stats), sizeof(gp_walk_desc)); return 0;}
+ sizeof(gp_autotune_entry), sizeof(gp_serve_config), sizeof(gp_serve_stats), sizeof(gp_walk_desc), sizeof(gp_loop_desc)); return 0;}
 '''
     import tempfile
     with tempfile.TemporaryDirectory() as d:
@@ -73,7 +73,7 @@ int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n
     py = [ctypes.sizeof(t) for t in (gp.gp_config, gp.gp_index_buf, gp.gp_vertex_buf, gp.gp_out_buf,
                                      gp.gp_uniforms_mvp, gp.gp_uniforms_skin, gp.gp_uniforms_envelope,
                                      gp.gp_stats_t, gp.gp_draw_desc, gp.gp_draw_config, gp.gp_autotune_entry,
-                                     gp.gp_serve_config, gp.gp_serve_stats, gp.gp_walk_desc)]
+                                     gp.gp_serve_config, gp.gp_serve_stats, gp.gp_walk_desc, gp.gp_loop_desc)]
     assert sizes == py
 
 
