@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(512, 2) batched_kernel(const __grid_constant__
                                      a.hash_slots, a.sort_n, a.out_chunk);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.off_bars);
   uint32_t* misc = reinterpret_cast<uint32_t*>(smem + L.off_misc);  // [0] unique counter, [8..] scan
+  uint32_t* wrange = misc + 48;  // [2 buf + 0/1]: triangle range of the window in flight into buffer buf
   uint32_t* idxbuf = reinterpret_cast<uint32_t*>(smem + L.off_idx);
   uint16_t* mapbuf = reinterpret_cast<uint16_t*>(smem + L.off_map);
   uint16_t* densebuf = reinterpret_cast<uint16_t*>(smem + L.off_dense);
@@ -131,7 +132,6 @@ __global__ void __launch_bounds__(512, 2) batched_kernel(const __grid_constant__
     for (uint32_t i = tid; i < 768; i += NT) palette[i] = u.palette[i];
   if (DEDUP != DEDUP_SORT)
     for (uint32_t s = tid; s < a.hash_slots; s += NT) S.table[s] = kEmpty;
-  __syncthreads();
 
   auto batch_range = [&](uint32_t b, uint32_t& t0, uint32_t& t1) {
     if (DYN) {
@@ -143,10 +143,13 @@ __global__ void __launch_bounds__(512, 2) batched_kernel(const __grid_constant__
     }
   };
   // Bulk-copies the 16-byte-aligned superset of the batch's index window
-  // (clipped to the 16-byte-granular part of the buffer).  Thread 0 only.
+  // (clipped to the 16-byte-granular part of the buffer) and records the
+  // batch's triangle range for the other threads.  Thread 0 only.
   auto issue_window = [&](uint32_t b, uint32_t buf) {
     uint32_t t0, t1;
     batch_range(b, t0, t1);
+    wrange[2 * buf] = t0;
+    wrange[2 * buf + 1] = t1;
     const uint32_t i0 = 3 * t0, i1 = 3 * t1, base = i0 & ~3u;
     const uint32_t end = min((i1 + 3) & ~3u, n4);
     // a window larger than the buffer is refused here and flagged by the consumer
@@ -160,7 +163,9 @@ __global__ void __launch_bounds__(512, 2) batched_kernel(const __grid_constant__
   bool aborted = false, window_inflight = false, window_timed_out = false;
   uint32_t inflight_buf = 0, waited_buf = 0;
   uint32_t U_cur = 0, U_next = 0;
+  uint32_t cur_t0 = 0, cur_t1 = 0;  // the current batch's triangles (the previous iteration's next batch)
   if (tid == 0) issue_window(blockIdx.x, 0);
+  __syncthreads();  // barriers initialised, table cleared, first window range recorded
   // iteration 'it': the current batch is blockIdx.x + (it - 1) G (none for
   // it == 0), the next one blockIdx.x + it G; their buffers alternate.
   for (uint32_t it = 0;; ++it) {
@@ -172,9 +177,11 @@ __global__ void __launch_bounds__(512, 2) batched_kernel(const __grid_constant__
     // --- A: the next batch's index window
     uint32_t n = 0, i0 = 0, base = 0;
     bool bad = false;
+    uint32_t nt0 = 0, nt1 = 0;
     if (has_next) {
-      uint32_t t0, t1;
-      batch_range(nxt, t0, t1);
+      nt0 = wrange[2 * nbuf];
+      nt1 = wrange[2 * nbuf + 1];
+      const uint32_t t0 = nt0, t1 = nt1;
       i0 = 3 * t0;
       n = 3 * (t1 - t0);
       base = i0 & ~3u;
@@ -290,8 +297,7 @@ __global__ void __launch_bounds__(512, 2) batched_kernel(const __grid_constant__
     if (tid == 0) *S.ucount = 0;
     // --- D: the current batch's triangles, in input order, chunk by chunk
     if (has_cur) {
-      uint32_t t0, t1;
-      batch_range(cur, t0, t1);
+      const uint32_t t0 = cur_t0, t1 = cur_t1;
       const CornerRank<DEDUP> rank{mapbuf + cbuf * L.map_elems, densebuf + cbuf * a.hash_slots, U_cur};
       for (uint32_t ta = t0; ta < t1; ta += a.out_chunk) {
         const uint32_t tb = min(ta + a.out_chunk, t1);
@@ -330,6 +336,8 @@ __global__ void __launch_bounds__(512, 2) batched_kernel(const __grid_constant__
       }
     }
     U_cur = U_next;
+    cur_t0 = nt0;
+    cur_t1 = nt1;
     if (!has_next) break;
   }
   if (aborted) {
