@@ -427,6 +427,10 @@ gp_status enqueue_draw(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* v
     return fail(c, GP_ERR_UNSUPPORTED, "hash_slots may be at most 32768");
   a.hash_bits = log2u(a.hash_slots);
   a.sort_n = next_pow2(a.max_batch_idx);
+  {  // 32-bit sort keys when every id (plus one value for "out of range") fits beside the position
+    const uint32_t pb = std::max(1u, log2u(a.sort_n));
+    a.sort_pos_bits = (pb < 32 && (uint64_t)a.num_verts + 1 < (1ull << (32 - pb))) ? pb : 0u;
+  }
   // staging for the output: the largest chunk (the whole batch, or a half,
   // quarter, ... of it) that keeps the most blocks resident on an SM, up to
   // four (beyond that the registers limit them)

@@ -150,12 +150,12 @@ __device__ __forceinline__ void load_raw(const unsigned char* row, VertexIn& v) 
 // One compare-exchange of the bitonic network seen from element i holding x,
 // whose partner (i ^ j) holds y: ascending runs where (i & k) == 0; the lower
 // index of a pair keeps the smaller key in an ascending run.
-__device__ __forceinline__ unsigned long long bitonic_keep(unsigned long long x, unsigned long long y, uint32_t i,
-                                                           uint32_t j, uint32_t k) {
+template <class T>
+__device__ __forceinline__ T bitonic_keep(T x, T y, uint32_t i, uint32_t j, uint32_t k) {
   const bool asc = (i & k) == 0;
   const bool lower = (i & j) == 0;
   const bool take_min = lower == asc;
-  const unsigned long long mn = x < y ? x : y, mx = x < y ? y : x;
+  const T mn = x < y ? x : y, mx = x < y ? y : x;
   return take_min ? mn : mx;
 }
 
@@ -166,11 +166,10 @@ __device__ __forceinline__ unsigned long long bitonic_keep(unsigned long long x,
 // network runs in shared memory; for j <= 32 the pairs touched by one warp
 // stay inside that warp's 64-key blocks (i = 2t - (t mod j), t = 32q + r), so
 // those stages need only a warp barrier.  Leaves the sorted keys in keys[].
-template <class Sync>
-__device__ __forceinline__ void bitonic_sort(unsigned long long* keys, uint32_t N, uint32_t tid, uint32_t NT,
-                                             Sync sync) {
+template <class T, class Sync>
+__device__ __forceinline__ void bitonic_sort(T* keys, uint32_t N, uint32_t tid, uint32_t NT, Sync sync) {
   if (N == 4 * NT) {
-    unsigned long long r[4];
+    T r[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) r[e] = keys[4 * tid + e];
     for (uint32_t k = 2; k <= N; k <<= 1) {
@@ -189,17 +188,17 @@ __device__ __forceinline__ void bitonic_sort(unsigned long long* keys, uint32_t 
           const uint32_t lm = j >> 2;
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            const unsigned long long y = __shfl_xor_sync(kFull, r[e], lm);
+            const T y = __shfl_xor_sync(kFull, r[e], lm);
             r[e] = bitonic_keep(r[e], y, 4 * tid + e, j, k);
           }
         } else if (j == 2) {
-          unsigned long long s[4];
+          T s[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) s[e] = bitonic_keep(r[e], r[e ^ 2], 4 * tid + e, 2, k);
 #pragma unroll
           for (int e = 0; e < 4; ++e) r[e] = s[e];
         } else {
-          unsigned long long s[4];
+          T s[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e) s[e] = bitonic_keep(r[e], r[e ^ 1], 4 * tid + e, 1, k);
 #pragma unroll
@@ -219,7 +218,7 @@ __device__ __forceinline__ void bitonic_sort(unsigned long long* keys, uint32_t 
         const uint32_t i = 2 * t - (t & (j - 1));
         const uint32_t l = i + j;
         const bool up = (i & k) == 0;
-        const unsigned long long x = keys[i], y = keys[l];
+        const T x = keys[i], y = keys[l];
         if ((x > y) == up) {
           keys[i] = y;
           keys[l] = x;
@@ -231,6 +230,59 @@ __device__ __forceinline__ void bitonic_sort(unsigned long long* keys, uint32_t 
     }
   }
   sync();
+}
+
+// Algorithm 2 on keys of type T = (id << pb) | position: sort, tail flags,
+// exclusive prefix sum.  pb = 32 with 64-bit keys; with 32-bit keys ids must
+// stay below 2^(32 - pb) - 1, the id field's largest value standing for an
+// id out of range (the host picks 32-bit keys when the vertex count allows
+// it: half the registers and shuffles of the sorting network).
+template <class T, class Sync, class Consume>
+__device__ __forceinline__ void sort_dedup(const DrawArgs& a, const BatchSmem& S, const uint32_t* ids, uint32_t n,
+                                           uint32_t tid, uint32_t NT, Sync sync, const Consume& consume,
+                                           uint32_t pb) {
+  const uint32_t lane = lane_id(), warp = tid >> 5;
+  T* keys = reinterpret_cast<T*>(S.keys);
+  const T invalid = (T)((sizeof(T) == 4 ? (1ull << (32 - pb)) - 1 : (unsigned long long)kInvalidId));
+  auto id_of = [&](T key) { return (uint32_t)(key >> pb); };
+  for (uint32_t i = tid; i < a.sort_n; i += NT) {
+    if (i < n) {
+      const uint32_t id = ids[i];
+      keys[i] = ((id < a.num_verts ? (T)id : invalid) << pb) | (T)i;
+    } else {
+      keys[i] = ~(T)0;
+    }
+  }
+  sync();
+  bitonic_sort(keys, a.sort_n, tid, NT, sync);
+  // tail flags over each thread's contiguous run, then a group scan with one
+  // barrier: every thread adds up the totals of the warps before its own
+  const uint32_t ipt = (n + NT - 1) / NT;
+  const uint32_t lo = min(tid * ipt, n), hi = min(lo + ipt, n);
+  uint32_t cnt = 0;
+  for (uint32_t i = lo; i < hi; ++i) cnt += (i == n - 1 || id_of(keys[i]) != id_of(keys[i + 1])) ? 1u : 0u;
+  const uint32_t inc = warp_inclusive_scan(cnt);
+  if (lane == 31) S.wsum[warp] = inc;
+  sync();
+  uint32_t r = inc - cnt;
+  for (uint32_t w = 0; w < warp; ++w) r += S.wsum[w];
+  if (tid == NT - 1) *S.ucount = r + cnt;
+  // the warp's ranks are contiguous: lane 0's first to lane 31's last
+  const uint32_t rb = __shfl_sync(kFull, r, 0), re = __shfl_sync(kFull, r + cnt, 31);
+  const T pmask = (T)((1ull << (sizeof(T) == 4 ? pb : 16)) - 1);
+  for (uint32_t i = lo; i < hi; ++i) {
+    const T key = keys[i];
+    const uint32_t id = id_of(key);
+    S.map[(uint32_t)(key & pmask)] = (uint16_t)r;
+    if (i == n - 1 || id != id_of(keys[i + 1])) {  // tail of an id's group
+      if (r < a.ucap) S.uniq[r] = (T)id == invalid ? kInvalidId : id;
+      else atomicOr(a.err, EBIT_CAPACITY);
+      ++r;
+    }
+  }
+  __syncwarp();
+  consume(rb, re, lane);
+  __syncwarp();
 }
 
 // Finds the unique indices of ids[0..n) and passes each new one, once, to
@@ -249,45 +301,8 @@ __device__ __forceinline__ void dedup(const DrawArgs& a, const BatchSmem& S, con
   const uint32_t lane = lane_id(), warp = tid >> 5;
   if (DEDUP == DEDUP_SORT) {
     // --- Algorithm 2: sort (id, position), tail flags, exclusive prefix sum
-    for (uint32_t i = tid; i < a.sort_n; i += NT) {
-      if (i < n) {
-        uint32_t id = ids[i];
-        id = id < a.num_verts ? id : kInvalidId;
-        S.keys[i] = ((unsigned long long)id << 32) | i;
-      } else {
-        S.keys[i] = ~0ull;
-      }
-    }
-    sync();
-    bitonic_sort(S.keys, a.sort_n, tid, NT, sync);
-    // tail flags over each thread's contiguous run, then a group scan with one
-    // barrier: every thread adds up the totals of the warps before its own
-    const uint32_t ipt = (n + NT - 1) / NT;
-    const uint32_t lo = min(tid * ipt, n), hi = min(lo + ipt, n);
-    uint32_t cnt = 0;
-    for (uint32_t i = lo; i < hi; ++i)
-      cnt += (i == n - 1 || (uint32_t)(S.keys[i] >> 32) != (uint32_t)(S.keys[i + 1] >> 32)) ? 1u : 0u;
-    const uint32_t inc = warp_inclusive_scan(cnt);
-    if (lane == 31) S.wsum[warp] = inc;
-    sync();
-    uint32_t r = inc - cnt;
-    for (uint32_t w = 0; w < warp; ++w) r += S.wsum[w];
-    if (tid == NT - 1) *S.ucount = r + cnt;
-    // the warp's ranks are contiguous: lane 0's first to lane 31's last
-    const uint32_t rb = __shfl_sync(kFull, r, 0), re = __shfl_sync(kFull, r + cnt, 31);
-    for (uint32_t i = lo; i < hi; ++i) {
-      const unsigned long long key = S.keys[i];
-      const uint32_t id = (uint32_t)(key >> 32);
-      S.map[(uint32_t)(key & 0xFFFFu)] = (uint16_t)r;
-      if (i == n - 1 || id != (uint32_t)(S.keys[i + 1] >> 32)) {  // tail of an id's group
-        if (r < a.ucap) S.uniq[r] = id;
-        else atomicOr(a.err, EBIT_CAPACITY);
-        ++r;
-      }
-    }
-    __syncwarp();
-    consume(rb, re, lane);
-    __syncwarp();
+    if (a.sort_pos_bits) sort_dedup<uint32_t>(a, S, ids, n, tid, NT, sync, consume, a.sort_pos_bits);
+    else sort_dedup<unsigned long long>(a, S, ids, n, tid, NT, sync, consume, 32);
   } else {
     // --- Algorithm 3 / Section 3.4: every index tries to store its id in its
     // home slot with atomicCAS and probes on after a collision (hash: linear,

@@ -63,6 +63,7 @@ struct DrawArgs {
   uint32_t hash_slots;           // power of two
   uint32_t hash_bits;            // log2(hash_slots)
   uint32_t sort_n;               // power of two >= max_batch_idx
+  uint32_t sort_pos_bits;        // sort: 32-bit keys (id << bits | position) with this many position bits; 0 = 64-bit
   uint32_t probe_k;
   uint32_t out_chunk;            // triangles per output bulk store (staging buffer size)
   // bookkeeping
