@@ -510,10 +510,11 @@ def walk_section(gp, torch, args):
 
 def loop_section(gp, torch, args):
     """One Loop subdivision step (Section 5.2) on synthetic meshes the size of
-    the paper's sphere and buddha: naive, sort (static batches of 768, 256
-    threads) and hash / parallel hash (dynamic batches of up to 192 indices
-    and 64 unique vertices, 64 threads), the paper's best settings; CUDA
-    events, adjacency built once beforehand."""
+    the paper's sphere and buddha: naive, warp voting (static batches of 96,
+    two warps per block), sort (static batches of 768, 256 threads) and hash /
+    parallel hash (dynamic batches of up to 192 indices and 64 unique
+    vertices, 64 threads), the paper's best settings; CUDA events, adjacency
+    built once beforehand."""
     res = {}
     for label, f in (("sphere-sized f=64", 64), ("buddha-sized f=233", 233)):
         mesh = mg.geodesic_sphere(f, 2)
@@ -529,7 +530,8 @@ def loop_section(gp, torch, args):
         gp.gp_partition_starts(ctx, h, starts)
         count = torch.tensor([nb], dtype=torch.int32, device="cuda")
         row = {"triangles": mesh.num_tris}
-        for name, variant, kw in (("naive", "naive", {}), ("sort_s768", "sort", {"batch_indices": 768}),
+        for name, variant, kw in (("naive", "naive", {}), ("warp_s96", "warp", {"batch_indices": 96, "threads": 64}),
+                                  ("sort_s768", "sort", {"batch_indices": 768}),
                                   ("hash_dyn192", "hash", {"starts": starts, "num_batches": count, "max_batches": nb,
                                                            "max_batch_indices": 192, "max_unique": 64,
                                                            "threads": 64}),

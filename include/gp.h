@@ -524,9 +524,10 @@ gp_status gp_loop_adjacency(const uint32_t* indices, uint64_t num_indices, uint3
  *         the midpoint.
  * Positions are the first three floats of each vertex row.  The vertex rule
  * reads a whole ring, so it is what the methods reuse: GP_NAIVE evaluates it
- * per corner; GP_SORT / GP_HASH / GP_PHASH evaluate it once per unique vertex
- * of a batch (static batches of batch_indices, or the dynamic batches of a
- * partition passed in d_starts).  All device buffers are caller-owned; the
+ * per corner; GP_WARP once per vertex of each round of Algorithm 1 (one warp
+ * per static batch of batch_indices <= 384 [96]); GP_SORT / GP_HASH /
+ * GP_PHASH once per unique vertex of a batch (static batches of
+ * batch_indices, or the dynamic batches of a partition passed in d_starts).  All device buffers are caller-owned; the
  * call enqueues on `stream` and returns. */
 typedef struct gp_loop_desc {
   const uint32_t* d_indices;         /* [num_indices], 16-byte aligned */
@@ -542,12 +543,13 @@ typedef struct gp_loop_desc {
   void* stream;                      /* cudaStream_t */
   uint64_t num_indices, num_vertices, ring_count;
   uint32_t stride_bytes;             /* >= 12, a multiple of 4 */
-  int32_t variant;                   /* GP_NAIVE, GP_SORT, GP_HASH or GP_PHASH */
-  uint32_t batch_indices;            /* static: indices per batch, a multiple of 3, <= 4095 [768] */
+  int32_t variant;                   /* GP_NAIVE, GP_WARP, GP_SORT, GP_HASH or GP_PHASH */
+  uint32_t batch_indices;            /* static: indices per batch, a multiple of 3, <= 4095 [768; warp: 96] */
   uint32_t max_batch_indices;        /* dynamic: 3 x the partition's triangle limit */
   uint32_t max_unique;               /* dynamic: the partition's unique limit [max_batch_indices] */
   uint32_t max_batches;              /* dynamic: the number of batches (or more) */
-  uint32_t threads;                  /* sort/hash/phash: threads per block, a power of two <= 512 [256] */
+  uint32_t threads;                  /* sort/hash/phash: threads per block, a power of two <= 512 [256];
+                                        warp: a multiple of 32 <= 256 [64] */
 } gp_loop_desc;
 
 /* GP_ERR_INVALID for bad sizes, pointers, variants or batch limits. */

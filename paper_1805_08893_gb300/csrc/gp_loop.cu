@@ -9,6 +9,9 @@
 // midpoint).  The vertex rule reads a whole 1-ring, so it is the "vertex
 // shader" the reuse methods share:
 //   naive            -- every triangle evaluates its three vertices itself;
+//   warp             -- Algorithm 1's rounds on static batches, one warp per
+//                       batch: the lanes holding a round's vertices evaluate
+//                       the rule, the round's triangles gather it by shuffles;
 //   sort/hash/phash  -- one thread block per batch (static, or the dynamic
 //                       batches of the partition) runs the shared dedup body;
 //                       each unique vertex's rule is evaluated once into
@@ -21,6 +24,7 @@
 
 #include "gp.h"
 #include "gp_batch_body.cuh"
+#include "gp_warp_body.cuh"
 
 namespace gp {
 
@@ -213,6 +217,63 @@ __global__ void __launch_bounds__(512) loop_batched_kernel(const __grid_constant
   }
 }
 
+// Algorithm 1 per warp: per-warp shared memory held[32] | ids[S] | map[S].
+__host__ __device__ inline uint32_t loop_warp_bytes(uint32_t S) { return 128 + ((S + 3) & ~3u) * 4 + ((S + 15) & ~15u); }
+
+__global__ void __launch_bounds__(256) loop_warp_kernel(const __grid_constant__ LoopArgs la, uint32_t S,
+                                                        uint32_t nbatches) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const uint32_t lane = lane_id(), warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  unsigned char* wp = smem + warp * loop_warp_bytes(S);
+  uint32_t* held = reinterpret_cast<uint32_t*>(wp);
+  uint32_t* widx = held + 32;
+  unsigned char* map = reinterpret_cast<unsigned char*>(widx + ((S + 3) & ~3u));
+  unsigned long long inv = 0, nb = 0;
+  for (uint32_t b = blockIdx.x * wpb + warp; b < nbatches; b += gridDim.x * wpb) {
+    const uint32_t B0 = b * S, n = min(B0 + S, 3 * la.num_tris) - B0;
+    for (uint32_t i = lane; i < n; i += 32) {
+      const uint32_t id = __ldg(la.idx + B0 + i);
+      widx[i] = id < la.num_verts ? id : kInvalidId;
+    }
+    __syncwarp();
+    for (uint32_t c = 0; c < n;) {
+      uint32_t fill, done;
+      warp_vote_round(widx, n, c, held, map, lane, fill, done);
+      const uint32_t tris = done / 3;
+      if (tris == 0) {  // cannot happen: a round's first chunk always places its lanes
+        if (lane == 0) atomicOr(la.counters + 2, (unsigned long long)EBIT_CAPACITY);
+        break;
+      }
+      float3 E = make_float3(0.f, 0.f, 0.f), P = E;
+      if (lane < fill) {
+        E = loop_even(la, held[lane]);
+        P = loop_pos(la, held[lane]);
+      }
+      inv += fill;
+      const uint32_t tfirst = (B0 + c) / 3;
+      for (uint32_t p = 0; p < tris; p += 32) {
+        const uint32_t j = p + lane;
+        const bool live = j < tris;
+        float3 Ec[3], Pc[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const uint32_t sl = live ? map[3 * j + k] : 0u;
+          Ec[k] = make_float3(__shfl_sync(kFull, E.x, sl), __shfl_sync(kFull, E.y, sl), __shfl_sync(kFull, E.z, sl));
+          Pc[k] = make_float3(__shfl_sync(kFull, P.x, sl), __shfl_sync(kFull, P.y, sl), __shfl_sync(kFull, P.z, sl));
+        }
+        if (live) loop_emit(la, tfirst + j, Ec, Pc);
+      }
+      __syncwarp();  // the next round overwrites held/map
+      c += 3 * tris;
+    }
+    ++nb;
+  }
+  if (lane == 0 && nb) {
+    atomicAdd(la.counters + 0, inv);
+    atomicAdd(la.counters + 1, nb);
+  }
+}
+
 size_t loop_batched_smem(int dedup, uint32_t cap, uint32_t ucap, uint32_t slots, uint32_t sort_n) {
   size_t o = (size_t)cap * 4 + (size_t)((cap + 1) & ~1u) * 2 + (size_t)ucap * 4 + (size_t)ucap * 24;
   o = (o + 15) & ~(size_t)15;
@@ -236,7 +297,7 @@ extern "C" gp_status gp_loop_subdivide(const gp_loop_desc* d) {
   // Section 5.2; see include/gp.h
   if (!d || !d->d_counters) return GP_ERR_INVALID;
   const int32_t v = d->variant;
-  if (v != GP_NAIVE && v != GP_SORT && v != GP_HASH && v != GP_PHASH) return GP_ERR_INVALID;
+  if (v != GP_NAIVE && v != GP_WARP && v != GP_SORT && v != GP_HASH && v != GP_PHASH) return GP_ERR_INVALID;
   if (d->num_indices % 3) return GP_ERR_INVALID;
   const uint32_t T = (uint32_t)(d->num_indices / 3);
   if (d->num_indices >= 0xFFFFFFF0ull) return GP_ERR_INVALID;
@@ -246,13 +307,15 @@ extern "C" gp_status gp_loop_subdivide(const gp_loop_desc* d) {
   if (reinterpret_cast<uintptr_t>(d->d_out) % 16 || d->stride_bytes < 12 || d->stride_bytes % 4)
     return GP_ERR_INVALID;
   const bool dyn = d->d_starts != nullptr;
-  if (v == GP_NAIVE && dyn) return GP_ERR_INVALID;
+  if ((v == GP_NAIVE || v == GP_WARP) && dyn) return GP_ERR_INVALID;
   if (dyn && (!d->d_num_batches || d->max_batch_indices == 0 || d->max_batch_indices % 3 || d->max_batches == 0))
     return GP_ERR_INVALID;
-  const uint32_t S = dyn ? d->max_batch_indices : (d->batch_indices ? d->batch_indices : 768);
-  if (S % 3 || S > 4095) return GP_ERR_INVALID;
-  const uint32_t threads = d->threads ? d->threads : 256;
-  if (v != GP_NAIVE && (threads % 32 || (threads & (threads - 1)) || threads > 512)) return GP_ERR_INVALID;
+  const uint32_t S = dyn ? d->max_batch_indices : (d->batch_indices ? d->batch_indices : (v == GP_WARP ? 96 : 768));
+  if (S % 3 || S > 4095 || (v == GP_WARP && S > kWarpMaxBatch)) return GP_ERR_INVALID;
+  const uint32_t threads = d->threads ? d->threads : (v == GP_WARP ? 64 : 256);
+  if (v == GP_WARP && (threads % 32 || threads > 256)) return GP_ERR_INVALID;
+  if (v != GP_NAIVE && v != GP_WARP && (threads % 32 || (threads & (threads - 1)) || threads > 512))
+    return GP_ERR_INVALID;
   if (T == 0) return GP_OK;
   cudaStream_t s = static_cast<cudaStream_t>(d->stream);
   LoopArgs la{};
@@ -270,6 +333,12 @@ extern "C" gp_status gp_loop_subdivide(const gp_loop_desc* d) {
   la.counters = d->d_counters;
   if (v == GP_NAIVE) {
     loop_naive_kernel<<<(T + 255) / 256, 256, 0, s>>>(la);
+    return cudaGetLastError() == cudaSuccess ? GP_OK : GP_ERR_CUDA;
+  }
+  if (v == GP_WARP) {
+    const uint32_t nbatches = (3 * T + S - 1) / S, wpb = threads / 32;
+    const size_t smem = (size_t)wpb * loop_warp_bytes(S);
+    loop_warp_kernel<<<(nbatches + wpb - 1) / wpb, threads, smem, s>>>(la, S, nbatches);
     return cudaGetLastError() == cudaSuccess ? GP_OK : GP_ERR_CUDA;
   }
   DrawArgs a{};

@@ -35,6 +35,43 @@ struct WarpSmem {
   }
 };
 
+// One round of Algorithm 1 over the batch's ids widx[0..n), starting at
+// index c: assigns each new id to the lowest free lane (held[lane] = id) in
+// index order until 32 lanes are held or the batch ends, and records for the
+// round's "done" indices (those before the first index that found no lane)
+// the lane holding their id (map[0..done)).  Every lane of the warp calls it.
+__device__ __forceinline__ void warp_vote_round(const uint32_t* widx, uint32_t n, uint32_t c, uint32_t* held,
+                                                unsigned char* map, uint32_t lane, uint32_t& fill_out,
+                                                uint32_t& done_out) {
+  uint32_t fill = 0, done = 0, off = c;
+  while (off < n && fill < 32) {
+    const uint32_t pos = off + lane;
+    const bool valid = pos < n;
+    const uint32_t x = valid ? widx[pos] : kEmpty;
+    int hs = -1;  // lane already holding x (earlier chunks of the round)
+    for (uint32_t h = 0; h < fill; ++h)
+      if (held[h] == x) hs = (int)h;
+    const uint32_t grp = __match_any_sync(kFull, x);
+    const uint32_t leader = __ffs(grp) - 1;
+    const bool is_new = valid && hs < 0 && leader == lane;
+    const uint32_t newmask = __ballot_sync(kFull, is_new);
+    const uint32_t rank = __popc(newmask & lanemask_lt());
+    const int myslot = (is_new && fill + rank < 32) ? (int)(fill + rank) : -1;
+    if (myslot >= 0) held[myslot] = x;
+    const int ls = __shfl_sync(kFull, myslot, leader);
+    const int slot = !valid ? -1 : (hs >= 0 ? hs : ls);
+    const uint32_t stop = __ballot_sync(kFull, slot < 0);
+    const uint32_t fb = stop ? (uint32_t)(__ffs(stop) - 1) : 32u;
+    if (lane < fb) map[done + lane] = (unsigned char)slot;
+    done += fb;
+    fill = min(32u, fill + __popc(newmask));
+    off += 32;
+    __syncwarp();
+  }
+  fill_out = fill;
+  done_out = done;
+}
+
 // Processes static batch b (indices [b*S, min((b+1)*S, 3T))) with the warp's
 // shared memory at wp; returns the shader invocations.
 template <int SH>
@@ -59,31 +96,8 @@ __device__ __forceinline__ uint32_t warp_vote_batch(const DrawArgs& a, const Uni
   uint32_t inv = 0;
   uint32_t c = 0;  // round start, relative to B0
   while (c < n) {
-    uint32_t fill = 0, done = 0, off = c;
-    while (off < n && fill < 32) {
-      const uint32_t pos = off + lane;
-      const bool valid = pos < n;
-      const uint32_t x = valid ? widx[pos] : kEmpty;
-      int hs = -1;  // lane already holding x (earlier chunks of the round)
-      for (uint32_t h = 0; h < fill; ++h)
-        if (held[h] == x) hs = (int)h;
-      const uint32_t grp = __match_any_sync(kFull, x);
-      const uint32_t leader = __ffs(grp) - 1;
-      const bool is_new = valid && hs < 0 && leader == lane;
-      const uint32_t newmask = __ballot_sync(kFull, is_new);
-      const uint32_t rank = __popc(newmask & lanemask_lt());
-      const int myslot = (is_new && fill + rank < 32) ? (int)(fill + rank) : -1;
-      if (myslot >= 0) held[myslot] = x;
-      const int ls = __shfl_sync(kFull, myslot, leader);
-      const int slot = !valid ? -1 : (hs >= 0 ? hs : ls);
-      const uint32_t stop = __ballot_sync(kFull, slot < 0);
-      const uint32_t fb = stop ? (uint32_t)(__ffs(stop) - 1) : 32u;
-      if (lane < fb) map[done + lane] = (unsigned char)slot;
-      done += fb;
-      fill = min(32u, fill + __popc(newmask));
-      off += 32;
-      __syncwarp();
-    }
+    uint32_t fill, done;
+    warp_vote_round(widx, n, c, held, map, lane, fill, done);
     const uint32_t tris = done / 3;
     if (tris == 0) {  // cannot happen: a round's first chunk always places its lanes
       if (lane == 0) atomicOr(a.err, EBIT_CAPACITY);

@@ -29,16 +29,20 @@ def _subdivide(mesh, variant, **kw):
 
 
 @pytest.mark.parametrize("which", ["sphere", "patch"])
-@pytest.mark.parametrize("variant,S", [("naive", 0), ("sort", 768), ("hash", 192), ("phash", 255), ("hash", 4095)])
+@pytest.mark.parametrize("variant,S", [("naive", 0), ("warp", 96), ("warp", 384), ("sort", 768), ("hash", 192),
+                                       ("phash", 255), ("hash", 4095)])
 def test_static_batches_match_oracle(which, variant, S):
     mesh = MESHES[which]
-    got, cnt = _subdivide(mesh, variant, batch_indices=S, threads=64 if S == 192 else 256)
+    threads = 64 if S == 192 or variant == "warp" else 256
+    got, cnt = _subdivide(mesh, variant, batch_indices=S, threads=threads)
     ref = L.subdivide(mesh.vertices[:, :3], mesh.indices)
     assert np.allclose(got, ref, rtol=1e-5, atol=1e-5)
     base, _ = _subdivide(mesh, "naive")
     assert np.array_equal(got.view(np.uint32), base.view(np.uint32))
     if variant == "naive":
         assert int(cnt[0]) == 3 * mesh.num_tris
+    elif variant == "warp":
+        assert int(cnt[0]) == int(B.batch_invocations(mesh.indices, B.static_starts(mesh.num_tris, S), "warp").sum())
     else:
         assert int(cnt[0]) == int(B.batch_invocations(mesh.indices, B.static_starts(mesh.num_tris, S), "hash").sum())
     assert int(cnt[2]) == 0
@@ -71,6 +75,6 @@ def test_bad_arguments():
     import torch
     import paper_1805_08893_gb300 as gp
     with pytest.raises(gp.GpError):
-        _subdivide(MESHES["sphere"], "warp")
+        _subdivide(MESHES["sphere"], "warp", batch_indices=387)  # above the warp batch limit
     with pytest.raises(gp.GpError):
         _subdivide(MESHES["sphere"], "hash", batch_indices=100)
