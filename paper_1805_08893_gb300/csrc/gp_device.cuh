@@ -106,8 +106,26 @@ __device__ __forceinline__ void shade_vertex(const Uniforms& u, const float* pal
     }
     mvp_transform(u, ps0, ps1, ps2, ns0, ns1, ns2, o);
   } else if (SH == 2) {
+    // four directions' Horner chains at a time (independent, so their
+    // latencies overlap); the terms are still summed in direction order
     float hsum = 0.f;
-    for (uint32_t j = 0; j < u.num_dirs; ++j) {
+    uint32_t j = 0;
+    for (; j + 4 <= u.num_dirs; j += 4) {
+      float s[4], h[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float* dq = u.dirs + 3 * (j + q);
+        s[q] = __fmul_rn(0.5f, __fmaf_rn(dq[0], v.px, __fmaf_rn(dq[1], v.py, __fmul_rn(dq[2], v.pz))));
+        h[q] = u.coef[kEnvelopeTerms - 1];
+      }
+#pragma unroll
+      for (int k = kEnvelopeTerms - 2; k >= 0; --k)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) h[q] = __fmaf_rn(h[q], s[q], u.coef[k]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) hsum = __fadd_rn(hsum, h[q]);
+    }
+    for (; j < u.num_dirs; ++j) {
       float s = __fmul_rn(0.5f, __fmaf_rn(u.dirs[3 * j], v.px,
                                           __fmaf_rn(u.dirs[3 * j + 1], v.py, __fmul_rn(u.dirs[3 * j + 2], v.pz))));
       float h = u.coef[kEnvelopeTerms - 1];
