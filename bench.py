@@ -597,8 +597,9 @@ def serving_section(gp, torch, args):
     gp.gp_server_wait(srv)
     gp.gp_server_stats(srv, reset=True)
     res = {}
-    for lam in (5000, 10000, 20000, 50000):
-        dur = 1.0
+    peak, peak_kind = load_peaks()
+    for lam in (5000, 10000, 20000, 50000, 100000, 200000, 500000):
+        dur = 1.0 if lam <= 50000 else 0.25
         arr = mg.poisson_arrivals(lam, lam, dur)
         pick = rng.integers(0, len(pool), size=arr.size)
         ids = gp.gp_server_replay(srv, arr, [mids[i] for i in pick],
@@ -607,7 +608,10 @@ def serving_section(gp, torch, args):
         gp.gp_server_wait(srv)
         st = gp.gp_server_stats(srv, reset=True)
         tris = st["triangles"]
+        # algorithmic bytes: indices, each vertex row once, the assembled triangles
+        algo = sum(12 * pool[i][0].num_tris + pool[i][0].vertices.nbytes + 84 * pool[i][0].num_tris for i in pick)
         res[str(lam)] = {"requests": int(arr.size), "triangles_per_s": tris / (st["wall_ms"] * 1e-3),
+                         "hbm_frac": algo / (st["wall_ms"] * 1e-3) / 1e9 / peak,
                          "offered_triangles_per_s": float(sum(pool[i][0].num_tris for i in pick) / dur),
                          "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
                          "device_busy_frac": st["busy_ms"] / max(st["wall_ms"], 1e-9), "steps": st["steps"]}

@@ -58,28 +58,35 @@ struct Request {
   float* d_out = nullptr;
   Clock::time_point arrival;
   Clock::time_point done_at;
-  uint32_t slot = 0;           // device uniform slot
-  bool uploaded = false;       // uniforms copied to the slot
+  uint32_t slot = 0;           // admission slot (at most max_active requests at once)
   uint32_t batches = 0, next = 0, done = 0;
   bool finished = false;
   gp_status status = GP_OK;
 };
 
+// A step's inputs travel to the device in one copy: the pinned host block
+// and the device block share one layout, packed per step as
+//   entries' FrameDraw | entries' Uniforms | item -> entry table | work
+//   counter (16 zero bytes) | DevRec (zeroed)
+// with each part 256-byte aligned.
 struct StepSlot {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  cudaEvent_t ev_uni = nullptr;  // after this slot's latest uniform uploads
-  FrameDraw* h_draws = nullptr;  // pinned
-  Uniforms* h_uni = nullptr;     // pinned staging for uniform uploads
-  FrameDraw* d_draws = nullptr;
-  uint32_t* h_item_draw = nullptr;  // pinned: work item -> entry
-  uint32_t* d_item_draw = nullptr;
-  uint32_t* d_work = nullptr;
-  DevRec* d_rec = nullptr;
-  DevRec* h_rec = nullptr;       // pinned
+  unsigned char* h_block = nullptr;  // pinned
+  unsigned char* d_block = nullptr;
+  size_t block_bytes = 0;
+  DevRec* h_rec = nullptr;           // pinned read-back of the step's record
   bool busy = false;
   std::vector<std::pair<uint64_t, uint32_t>> parts;  // (request, batches in this step)
 };
+
+inline size_t step_align(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Bytes of a step block for n entries and `items` work items.
+inline size_t step_block_bytes(uint32_t n, uint32_t items) {
+  return step_align(sizeof(FrameDraw) * n) + step_align(sizeof(Uniforms) * n) + step_align(4ull * items) + 256 +
+         step_align(sizeof(DevRec));
+}
 
 }  // namespace
 
@@ -104,7 +111,7 @@ struct gp_server {
   uint64_t next_req = 1;
   uint64_t submitted = 0, completed = 0;
   std::vector<uint32_t> free_slots;
-  Uniforms* d_uni = nullptr;
+  std::vector<uint32_t> item_scratch;  // launch_step's work item -> entry table
   std::vector<StepSlot> steps;
   int frame_bpsm = 1;
   // statistics
@@ -277,9 +284,13 @@ void admit(gp_server* s) {
 
 // Builds and launches one step on a free slot.  Called with s->mu held.
 bool launch_step(gp_server* s, StepSlot& st) {
-  uint32_t n = 0, items = 0, batches = 0, nuni = 0;
+  uint32_t n = 0, items = 0, batches = 0;
   st.parts.clear();
-  std::vector<std::pair<uint32_t, uint32_t>> uni_copies;  // (staging index, device slot)
+  // entries first (FrameDraw and Uniforms at capacity offsets), then packed
+  FrameDraw* h_draws = reinterpret_cast<FrameDraw*>(st.h_block);
+  Uniforms* h_uni = reinterpret_cast<Uniforms*>(st.h_block + step_align(sizeof(FrameDraw) * kStepMaxEntries));
+  std::vector<uint32_t>& item_draw = s->item_scratch;
+  item_draw.clear();
   for (uint64_t rid : s->active) {
     if (batches >= s->cfg.step_max_batches || n >= kStepMaxEntries) break;
     Request& r = s->reqs[rid];
@@ -287,7 +298,7 @@ bool launch_step(gp_server* s, StepSlot& st) {
     Mesh& m = s->meshes[r.mesh];
     const gp_draw_config& k = m.k;  // every request on a mesh uses its resident configuration
     const uint32_t take = std::min(r.batches - r.next, s->cfg.step_max_batches - batches);
-    FrameDraw& D = st.h_draws[n];
+    FrameDraw& D = h_draws[n];
     std::memset(&D, 0, sizeof(D));
     DrawArgs& a = D.a;
     a.idx = m.d_idx;
@@ -299,8 +310,6 @@ bool launch_step(gp_server* s, StepSlot& st) {
     a.vec8 = (reinterpret_cast<uintptr_t>(m.d_vtx) % 32 == 0 && m.stride % 32 == 0) ? 1u : 0u;
     a.out = r.d_out;
     a.probe_k = s->ctx->cfg.probe_k;
-    a.counters = st.d_rec->cnt;
-    a.err = &st.d_rec->err;
     D.method = k.variant == GP_NAIVE ? kFrameNaive
                : k.variant == GP_WARP ? kFrameWarp
                : k.variant == GP_SORT ? kFrameSort
@@ -325,42 +334,45 @@ bool launch_step(gp_server* s, StepSlot& st) {
     } else if (k.variant == GP_WARP) {
       a.static_batch_tris = k.batch_indices / 3;
     }
-    D.u = s->d_uni + r.slot;
+    h_uni[n] = r.uni;
     D.batch_begin = r.next;
     D.num_batches = take;
     const uint32_t per = D.method == kFrameNaive ? 1u : (D.method == kFrameWarp ? kFrameThreads / 32 : kFrameThreads / D.group);
     D.items = (take + per - 1) / per;
     D.item_begin = items;
-    for (uint32_t j = 0; j < D.items; ++j) st.h_item_draw[items + j] = n;
+    for (uint32_t j = 0; j < D.items; ++j) item_draw.push_back(n);
     items += D.items;
-    if (!r.uploaded) {
-      st.h_uni[nuni] = r.uni;
-      uni_copies.push_back({nuni, r.slot});
-      ++nuni;
-      r.uploaded = true;
-    }
     r.next += take;
     batches += take;
     st.parts.push_back({rid, take});
     ++n;
   }
   if (n == 0) return false;
+  // pack: move the uniforms down behind the n entries, then the item table,
+  // the zeroed work counter and record; point the entries at the device copy
+  const size_t o_uni = step_align(sizeof(FrameDraw) * n);
+  const size_t o_items = o_uni + step_align(sizeof(Uniforms) * n);
+  const size_t o_work = o_items + step_align(4ull * items);
+  const size_t o_rec = o_work + 256;
+  const size_t bytes = o_rec + sizeof(DevRec);
+  std::memmove(st.h_block + o_uni, h_uni, sizeof(Uniforms) * n);
+  std::memcpy(st.h_block + o_items, item_draw.data(), 4ull * items);
+  std::memset(st.h_block + o_work, 0, 256 + sizeof(DevRec));
+  const Uniforms* d_uni = reinterpret_cast<const Uniforms*>(st.d_block + o_uni);
+  DevRec* d_rec = reinterpret_cast<DevRec*>(st.d_block + o_rec);
+  for (uint32_t i = 0; i < n; ++i) {
+    h_draws[i].u = d_uni + i;
+    h_draws[i].a.counters = d_rec->cnt;
+    h_draws[i].a.err = &d_rec->err;
+  }
   cudaStream_t q = st.stream;
-  for (auto& uc : uni_copies)
-    cudaMemcpyAsync(s->d_uni + uc.second, st.h_uni + uc.first, sizeof(Uniforms), cudaMemcpyHostToDevice, q);
-  cudaEventRecord(st.ev_uni, q);
-  // a request admitted by an earlier step had its uniforms uploaded on that
-  // step's stream: order after every other slot's latest uploads
-  for (StepSlot& o : s->steps)
-    if (&o != &st) cudaStreamWaitEvent(q, o.ev_uni, 0);
   cudaEventRecord(st.ev0, q);
-  cudaMemcpyAsync(st.d_draws, st.h_draws, sizeof(FrameDraw) * n, cudaMemcpyHostToDevice, q);
-  cudaMemcpyAsync(st.d_item_draw, st.h_item_draw, sizeof(uint32_t) * items, cudaMemcpyHostToDevice, q);
-  cudaMemsetAsync(st.d_work, 0, 16, q);
-  cudaMemsetAsync(st.d_rec, 0, sizeof(DevRec), q);
+  cudaMemcpyAsync(st.d_block, st.h_block, bytes, cudaMemcpyHostToDevice, q);
   const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)s->ctx->sms * s->frame_bpsm, items));
-  cudaError_t e = launch_frame(st.d_draws, st.d_item_draw, items, st.d_work, st.d_rec->cnt, grid, q);
-  cudaMemcpyAsync(st.h_rec, st.d_rec, sizeof(DevRec), cudaMemcpyDeviceToHost, q);
+  cudaError_t e = launch_frame(reinterpret_cast<const FrameDraw*>(st.d_block),
+                               reinterpret_cast<const uint32_t*>(st.d_block + o_items), items,
+                               reinterpret_cast<uint32_t*>(st.d_block + o_work), d_rec->cnt, grid, q);
+  cudaMemcpyAsync(st.h_rec, d_rec, sizeof(DevRec), cudaMemcpyDeviceToHost, q);
   cudaEventRecord(st.ev1, q);
   if (e != cudaSuccess) s->last_error = GP_ERR_CUDA;
   st.busy = true;
@@ -429,15 +441,9 @@ void free_server(gp_server* s) {
     if (st.stream) cudaStreamDestroy(st.stream);
     if (st.ev0) cudaEventDestroy(st.ev0);
     if (st.ev1) cudaEventDestroy(st.ev1);
-    if (st.ev_uni) cudaEventDestroy(st.ev_uni);
-    if (st.h_draws) cudaFreeHost(st.h_draws);
-    if (st.h_uni) cudaFreeHost(st.h_uni);
+    if (st.h_block) cudaFreeHost(st.h_block);
+    if (st.d_block) cudaFree(st.d_block);
     if (st.h_rec) cudaFreeHost(st.h_rec);
-    if (st.d_draws) cudaFree(st.d_draws);
-    if (st.h_item_draw) cudaFreeHost(st.h_item_draw);
-    if (st.d_item_draw) cudaFree(st.d_item_draw);
-    if (st.d_work) cudaFree(st.d_work);
-    if (st.d_rec) cudaFree(st.d_rec);
   }
   for (auto& kv : s->meshes) {
     Mesh& m = kv.second;
@@ -449,7 +455,6 @@ void free_server(gp_server* s) {
     if (m.h_idx) cudaFreeHost(m.h_idx);
     if (m.h_vtx) cudaFreeHost(m.h_vtx);
   }
-  if (s->d_uni) cudaFree(s->d_uni);
   if (s->upload) cudaStreamDestroy(s->upload);
   delete s;
 }
@@ -543,23 +548,16 @@ gp_status gp_server_create(gp_ctx* c, const gp_serve_config* cfg_in, gp_server**
   s->k = k;
   cudaSetDevice(c->device);
   cudaError_t e = cudaStreamCreateWithFlags(&s->upload, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMalloc(&s->d_uni, sizeof(Uniforms) * cfg.max_active);
   s->steps.resize(cfg.streams);
   for (StepSlot& st : s->steps) {
     if (e != cudaSuccess) break;
     if ((e = cudaStreamCreateWithFlags(&st.stream, cudaStreamNonBlocking)) != cudaSuccess) break;
     if ((e = cudaEventCreate(&st.ev0)) != cudaSuccess) break;
     if ((e = cudaEventCreate(&st.ev1)) != cudaSuccess) break;
-    if ((e = cudaEventCreateWithFlags(&st.ev_uni, cudaEventDisableTiming)) != cudaSuccess) break;
-    if ((e = cudaEventRecord(st.ev_uni, st.stream)) != cudaSuccess) break;
-    if ((e = cudaMallocHost(&st.h_draws, sizeof(FrameDraw) * kStepMaxEntries)) != cudaSuccess) break;
-    if ((e = cudaMallocHost(&st.h_uni, sizeof(Uniforms) * kStepMaxEntries)) != cudaSuccess) break;
+    st.block_bytes = step_block_bytes(kStepMaxEntries, cfg.step_max_batches);
+    if ((e = cudaMallocHost(&st.h_block, st.block_bytes)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&st.d_block, st.block_bytes)) != cudaSuccess) break;
     if ((e = cudaMallocHost(&st.h_rec, sizeof(DevRec))) != cudaSuccess) break;
-    if ((e = cudaMalloc(&st.d_draws, sizeof(FrameDraw) * kStepMaxEntries)) != cudaSuccess) break;
-    if ((e = cudaMallocHost(&st.h_item_draw, sizeof(uint32_t) * cfg.step_max_batches)) != cudaSuccess) break;
-    if ((e = cudaMalloc(&st.d_item_draw, sizeof(uint32_t) * cfg.step_max_batches)) != cudaSuccess) break;
-    if ((e = cudaMalloc(&st.d_work, 16)) != cudaSuccess) break;
-    if ((e = cudaMalloc(&st.d_rec, sizeof(DevRec))) != cudaSuccess) break;
   }
   if (e != cudaSuccess) {
     free_server(s);
