@@ -53,7 +53,7 @@ typedef enum gp_status {
   GP_ERR_TIMEOUT = 4,      /* gp_sync timed out, or a bounded device wait gave up */
   GP_ERR_BUSY = 5,         /* admission refused: over the memory budget or queue full */
   GP_ERR_INDEX_RANGE = 6,  /* an index was >= num_vertices (or 0xFFFFFFFF) */
-  GP_ERR_UNSUPPORTED = 7   /* valid request this build cannot run */
+  GP_ERR_UNSUPPORTED = 7   /* a valid request the library cannot run (a capacity or limit) */
 } gp_status;
 
 /* Vertex-reuse method.  GP_NAIVE: Section 3.3 "statically batched naive";
