@@ -367,7 +367,10 @@ typedef struct gp_serve_stats {
 } gp_serve_stats;
 
 /* Starts a server (and its thread) on the context's device.  The context
- * must outlive the server. */
+ * must outlive the server.  GP_ERR_INVALID for a malformed configuration
+ * (threads_per_group of sort/hash/phash other than 64, 128 or 256);
+ * GP_ERR_UNSUPPORTED when a batch of the configuration does not fit the
+ * frame kernel's shared memory. */
 gp_status gp_server_create(gp_ctx* ctx, const gp_serve_config* cfg, gp_server** out);
 
 /* Registers a mesh: the host buffers are copied; the mesh is uploaded on

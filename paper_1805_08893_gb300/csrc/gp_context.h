@@ -56,6 +56,12 @@ struct Partition {
   uint64_t count = 0;
 };
 
+// Capacities of a sort/hash/phash frame draw whose max_batch_idx, ucap and
+// num_verts are set: hash table, sort keys and, when the group is the whole
+// block (the pipelined path), the output chunk.  Returns the shared memory
+// its groups need in a block (at most kFrameSliceBytes to run), 0 if a
+// batch cannot run that way.
+uint32_t frame_capacities(DrawArgs& a, int method, uint32_t shader, uint32_t group);
 uint32_t next_pow2(uint32_t x);
 uint32_t log2u(uint32_t x);
 const char* status_name(gp_status s);

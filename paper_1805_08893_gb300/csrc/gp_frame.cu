@@ -7,12 +7,19 @@
 //   naive -- one group of 256 threads, one triangle per thread (Section 3.3);
 //   warp  -- eight warps, each runs one static batch by warp voting
 //            (Algorithm 1);
-//   sort / hash / phash -- 256/G groups, each runs one batch (static, or a
-//            dynamic batch from the draw's partition) through the same
-//            dedup-and-shade body as the single-draw kernel.
+//   sort / hash / phash, G < 256 -- 256/G groups, each runs one batch
+//            (static, or a dynamic batch from the draw's partition) through
+//            the dedup-and-shade body of gp_batch_body.cuh;
+//   sort / hash / phash, G = 256 -- the whole block runs the batches of
+//            consecutive items of the draw through the two-stage pipeline of
+//            the single-draw kernel (gp_batch_pipeline.cuh).
 // Each group works in its own slice of the block's shared memory, assembles
-// its triangles there and writes them with 16-byte streaming stores.
-#include "gp_batch_body.cuh"
+// its triangles there and writes them with 16-byte streaming stores (the
+// pipeline: bulk stores).  The current draw's uniforms (and palette) are
+// copied into shared memory when the draw changes.
+#include <cstddef>
+
+#include "gp_batch_pipeline.cuh"
 #include "gp_warp_body.cuh"
 
 namespace gp {
@@ -76,8 +83,7 @@ __device__ __forceinline__ void store_staged(float* dst, const float* src, uint3
 }
 
 template <int SH>
-__device__ __noinline__ uint2 frame_naive(const FrameDraw& D, uint32_t b, unsigned char* slices,
-                                          const float* palette) {
+__device__ __noinline__ uint2 frame_naive(const FrameDraw& D, const Uniforms& u, uint32_t b, unsigned char* slices) {
   constexpr int K = ShaderTraits<SH>::K;
   constexpr int F = 3 * K;
   const DrawArgs& a = D.a;
@@ -99,7 +105,7 @@ __device__ __noinline__ uint2 frame_naive(const FrameDraw& D, uint32_t b, unsign
     for (int k = 0; k < 3; ++k) {
       const uint32_t id = __ldg(a.idx + 3u * t + k);
       float o[K];
-      fetch_and_shade<SH>(a, *D.u, palette, id, o);
+      fetch_and_shade<SH>(a, u, u.palette, id, o);
 #pragma unroll
       for (int c = 0; c < K; ++c) stage[lane * F + k * K + c] = o[c];
       if (a.corner_ids != nullptr) a.corner_ids[3u * t + k] = id;
@@ -111,23 +117,22 @@ __device__ __noinline__ uint2 frame_naive(const FrameDraw& D, uint32_t b, unsign
 }
 
 template <int SH>
-__device__ __noinline__ uint2 frame_warp(const FrameDraw& D, uint32_t item, unsigned char* slices,
-                                         const float* palette) {
+__device__ __noinline__ uint2 frame_warp(const FrameDraw& D, const Uniforms& u, uint32_t item, unsigned char* slices) {
   const DrawArgs& a = D.a;
   const uint32_t warp = threadIdx.x >> 5, lane = lane_id();
   const uint32_t j = item * (kFrameThreads / 32) + warp;
   if (j >= D.num_batches) return make_uint2(0, 0);
   const uint32_t b = D.batch_begin + j;
   unsigned char* wp = slices + warp * WarpSmem<SH>::per_warp_bytes(3u * a.static_batch_tris);
-  const uint32_t n = warp_vote_batch<SH>(a, *D.u, palette, b, wp, lane);
+  const uint32_t n = warp_vote_batch<SH>(a, u, u.palette, b, wp, lane);
   if (lane != 0) return make_uint2(0, 0);
   if (a.batch_inv != nullptr && b < a.batch_cap) a.batch_inv[b] = n;
   return make_uint2(n, 1u);
 }
 
 template <int METHOD, int SH>
-__device__ __noinline__ uint2 frame_group(const FrameDraw& D, uint32_t item, unsigned char* slices,
-                                          const float* palette) {
+__device__ __noinline__ uint2 frame_group(const FrameDraw& D, const Uniforms& u, uint32_t item,
+                                          unsigned char* slices) {
   constexpr int DEDUP = METHOD == kFrameSort ? DEDUP_SORT : (METHOD == kFrameHash ? DEDUP_HASH : DEDUP_PHASH);
   constexpr int K = ShaderTraits<SH>::K;
   constexpr int KS = ShaderTraits<SH>::KS;
@@ -172,7 +177,7 @@ __device__ __noinline__ uint2 frame_group(const FrameDraw& D, uint32_t item, uns
     for (uint32_t s = gt; s < a.hash_slots; s += G) S.table[s] = kEmpty;
   if (gt == 0) *S.ucount = 0;
   sync();
-  dedup_and_shade<DEDUP, SH>(a, *D.u, palette, S, win, n, gt, G, sync);
+  dedup_and_shade<DEDUP, SH>(a, u, u.palette, S, win, n, gt, G, sync);
   sync();
   const uint32_t U = min(*S.ucount, a.ucap);
   const size_t g0 = (size_t)t0 * F;
@@ -188,14 +193,52 @@ __device__ __noinline__ uint2 frame_group(const FrameDraw& D, uint32_t item, uns
 // Per-method bodies are separate (not inlined) functions, each with its own
 // register allocation, so the heaviest path does not make every path spill.
 template <int SH>
-__device__ __forceinline__ uint2 frame_item(const FrameDraw& D, uint32_t item, unsigned char* slices,
-                                            const float* palette) {
+__device__ __forceinline__ uint2 frame_item(const FrameDraw& D, const Uniforms& u, uint32_t item,
+                                            unsigned char* slices) {
   switch (D.method) {
-    case kFrameNaive: return frame_naive<SH>(D, D.batch_begin + item, slices, palette);
-    case kFrameWarp: return frame_warp<SH>(D, item, slices, palette);
-    case kFrameSort: return frame_group<kFrameSort, SH>(D, item, slices, palette);
-    case kFrameHash: return frame_group<kFrameHash, SH>(D, item, slices, palette);
-    default: return frame_group<kFramePHash, SH>(D, item, slices, palette);
+    case kFrameNaive: return frame_naive<SH>(D, u, D.batch_begin + item, slices);
+    case kFrameWarp: return frame_warp<SH>(D, u, item, slices);
+    case kFrameSort: return frame_group<kFrameSort, SH>(D, u, item, slices);
+    case kFrameHash: return frame_group<kFrameHash, SH>(D, u, item, slices);
+    default: return frame_group<kFramePHash, SH>(D, u, item, slices);
+  }
+}
+
+// Shared memory of the pipelined path (the layout of the single-draw kernel
+// without its palette, which the frame keeps beside the uniforms).
+__host__ __device__ inline BatchLayout frame_pipe_layout(int dedup, int shader, const DrawArgs& a) {
+  const uint32_t K = shader == 2 ? 8u : 7u;
+  return batch_layout(dedup, K, K | 1u, shader == 1 ? 64u : 32u, false, a.max_batch_idx, a.ucap, a.hash_slots,
+                      a.sort_n, a.out_chunk);
+}
+
+// Batches [b0, b1) of a sort/hash/phash draw whose groups are the whole
+// block, through the pipeline.  Returns (unique vertices, batches) for
+// thread 0; (~0u, ~0u) on every thread after an aborted run.
+template <int DEDUP, int SH, bool DYN>
+__device__ __noinline__ uint2 frame_pipe(const FrameDraw& D, const Uniforms& u, unsigned char* slices, PipeBars& pb,
+                                         uint32_t b0, uint32_t b1) {
+  const BatchLayout L = frame_pipe_layout(DEDUP, SH, D.a);
+  unsigned long long inv = 0, nbat = 0;
+  if (!pipeline_run<DEDUP, SH, DYN>(D.a, u, u.palette, slices, L, pb, b0, 1u, b1, inv, nbat))
+    return make_uint2(~0u, ~0u);
+  return make_uint2((uint32_t)inv, (uint32_t)nbat);
+}
+
+template <int DEDUP, int SH>
+__device__ __forceinline__ uint2 frame_pipe_mode(const FrameDraw& D, const Uniforms& u, unsigned char* slices,
+                                                 PipeBars& pb, uint32_t b0, uint32_t b1) {
+  return D.dynamic ? frame_pipe<DEDUP, SH, true>(D, u, slices, pb, b0, b1)
+                   : frame_pipe<DEDUP, SH, false>(D, u, slices, pb, b0, b1);
+}
+
+template <int SH>
+__device__ __forceinline__ uint2 frame_pipe_any(const FrameDraw& D, const Uniforms& u, unsigned char* slices,
+                                                PipeBars& pb, uint32_t b0, uint32_t b1) {
+  switch (D.method) {
+    case kFrameSort: return frame_pipe_mode<DEDUP_SORT, SH>(D, u, slices, pb, b0, b1);
+    case kFrameHash: return frame_pipe_mode<DEDUP_HASH, SH>(D, u, slices, pb, b0, b1);
+    default: return frame_pipe_mode<DEDUP_PHASH, SH>(D, u, slices, pb, b0, b1);
   }
 }
 
@@ -211,53 +254,87 @@ __global__ void __launch_bounds__(kFrameThreads, 3) frame_kernel(const FrameDraw
                                                                  uint32_t total_items, uint32_t* work,
                                                                  unsigned long long* counters) {
   extern __shared__ __align__(128) unsigned char smem[];
-  float* palette = reinterpret_cast<float*>(smem);
-  unsigned char* slices = smem + 768 * 4;
+  Uniforms* su = reinterpret_cast<Uniforms*>(smem);  // the current draw's uniforms (and palette)
+  unsigned char* slices = smem + kFrameUniBytes;
   __shared__ uint32_t s_base;
   __shared__ __align__(16) FrameDraw s_draw;  // the current item's draw, read from shared memory
+  __shared__ __align__(8) uint64_t s_bars[2];  // index-window mbarriers of the pipelined path
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bars[0], 1);
+    mbar_init(&s_bars[1], 1);
+    fence_mbar_init();
+  }
+  PipeBars pb{s_bars, 0u, 0u};
   unsigned long long inv = 0, nbat = 0;
-  uint32_t pal_draw = 0xFFFFFFFFu, cur_draw = 0xFFFFFFFFu;
-  for (;;) {
+  uint32_t cur_draw = 0xFFFFFFFFu;
+  bool aborted = false;
+  while (!aborted) {
     if (threadIdx.x == 0) s_base = atomicAdd(work, kFrameChunk);
     __syncthreads();
     const uint32_t base = s_base;
     if (base >= total_items) break;
     const uint32_t end = min(base + kFrameChunk, total_items);
-    for (uint32_t item = base; item < end; ++item) {
+    for (uint32_t item = base; item < end;) {
       const uint32_t d = __ldg(item_draw + item);  // uniform across the block
       if (d != cur_draw) {
         constexpr uint32_t kWords = sizeof(FrameDraw) / 4;
         const uint32_t* src = reinterpret_cast<const uint32_t*>(draws + d);
         uint32_t* dst = reinterpret_cast<uint32_t*>(&s_draw);
         for (uint32_t i = threadIdx.x; i < kWords; i += blockDim.x) dst[i] = src[i];
+        // the uniforms; the palette only for skinning
+        const FrameDraw* dg = draws + d;
+        const uint32_t uw = (dg->shader == 1 ? sizeof(Uniforms) : offsetof(Uniforms, palette)) / 4;
+        const uint32_t* usrc = reinterpret_cast<const uint32_t*>(dg->u);
+        uint32_t* udst = reinterpret_cast<uint32_t*>(su);
+        for (uint32_t i = threadIdx.x; i < uw; i += blockDim.x) udst[i] = usrc[i];
         cur_draw = d;
         __syncthreads();
       }
       const FrameDraw& D = s_draw;
-      if (D.shader == 1 && pal_draw != d) {
-        for (uint32_t i = threadIdx.x; i < 768; i += blockDim.x) palette[i] = D.u->palette[i];
-        pal_draw = d;
-        __syncthreads();
-      }
+      const Uniforms& u = *su;
       const uint32_t local = item - D.item_begin;
       uint2 r;
-      switch (D.shader) {
-        case 0: r = frame_item<0>(D, local, slices, palette); break;
-        case 1: r = frame_item<1>(D, local, slices, palette); break;
-        case 2: r = frame_item<2>(D, local, slices, palette); break;
-        default: r = frame_item<3>(D, local, slices, palette); break;
+      if (D.method >= kFrameSort && D.group == kFrameThreads) {
+        // one batch per item: the chunk's items of this draw are one run
+        const uint32_t last = min(end, D.item_begin + D.items);
+        const uint32_t b0 = D.batch_begin + local, b1 = D.batch_begin + (last - D.item_begin);
+        switch (D.shader) {
+          case 0: r = frame_pipe_any<0>(D, u, slices, pb, b0, b1); break;
+          case 1: r = frame_pipe_any<1>(D, u, slices, pb, b0, b1); break;
+          case 2: r = frame_pipe_any<2>(D, u, slices, pb, b0, b1); break;
+          default: r = frame_pipe_any<3>(D, u, slices, pb, b0, b1); break;
+        }
+        if (r.x == ~0u && r.y == ~0u) {  // flagged in the draw's error word; the other blocks go on
+          aborted = true;
+          break;
+        }
+        item = last;
+      } else {
+        switch (D.shader) {
+          case 0: r = frame_item<0>(D, u, local, slices); break;
+          case 1: r = frame_item<1>(D, u, local, slices); break;
+          case 2: r = frame_item<2>(D, u, local, slices); break;
+          default: r = frame_item<3>(D, u, local, slices); break;
+        }
+        ++item;
       }
       inv += r.x;
       nbat += r.y;
       __syncthreads();  // the slices (and possibly the descriptor) are reused by the next item
     }
   }
+  if (threadIdx.x == 0) bulk_wait_all<0>();
   // per-thread partial counts (group leaders, warp leaders) into the record
   if (inv) atomicAdd(counters + CNT_INVOCATIONS, inv);
   if (nbat) atomicAdd(counters + CNT_BATCHES, nbat);
 }
 
-size_t frame_smem_bytes() { return 768 * 4 + kFrameSliceBytes; }
+size_t frame_smem_bytes() { return kFrameUniBytes + kFrameSliceBytes; }
+
+uint32_t frame_pipe_bytes(int method, int shader, const DrawArgs& a) {
+  const int dedup = method == kFrameSort ? DEDUP_SORT : (method == kFrameHash ? DEDUP_HASH : DEDUP_PHASH);
+  return frame_pipe_layout(dedup, shader, a).total;
+}
 
 int frame_blocks_per_sm() {
   const size_t smem = frame_smem_bytes();

@@ -38,6 +38,35 @@ struct gp_frame {
   uint64_t last_ticket = 0;
 };
 
+namespace gp {
+namespace rt {
+
+uint32_t frame_capacities(DrawArgs& a, int method, uint32_t shader, uint32_t group) {
+  const bool pipe = group == kFrameThreads;
+  // the whole-block path sizes its table like the single-draw kernel
+  a.hash_slots = pipe ? std::max(next_pow2(2 * a.ucap), std::min(next_pow2(4 * a.ucap), 1024u)) : next_pow2(2 * a.ucap);
+  a.hash_slots = std::max(a.hash_slots, next_pow2(group));
+  a.hash_bits = log2u(a.hash_slots);
+  a.sort_n = next_pow2(a.max_batch_idx);
+  {  // 32-bit sort keys when every id (plus one value for "out of range") fits beside the position
+    const uint32_t pb = std::max(1u, log2u(a.sort_n));
+    a.sort_pos_bits = (pb < 32 && (uint64_t)a.num_verts + 1 < (1ull << (32 - pb))) ? pb : 0u;
+  }
+  if (!pipe) return frame_slice_bytes(method, (int)shader, a.max_batch_idx, a.ucap, a.hash_slots, a.sort_n, group, 0);
+  // a thread numbers at most 32 positions; slots are stored in 15 bits
+  if (method != kFrameSort && (a.max_batch_idx > 32u * group || a.hash_slots > 32768u)) return 0;
+  // the largest output chunk (the whole batch, a half, a quarter, ...) that fits
+  for (uint32_t chunk = (a.max_batch_idx + 2) / 3;; chunk = (chunk + 1) / 2) {
+    a.out_chunk = chunk;
+    const uint32_t bytes = frame_pipe_bytes(method, (int)shader, a);
+    if (bytes <= kFrameSliceBytes) return bytes;
+    if (chunk <= 16) return 0;
+  }
+}
+
+}  // namespace rt
+}  // namespace gp
+
 namespace {
 
 int method_of(int32_t variant) {
@@ -102,12 +131,8 @@ gp_status capacities(gp_ctx* c, const gp_draw_config& k, uint32_t shader, DrawAr
     a.max_batch_idx = 3 * k.max_tris;
     a.ucap = k.max_unique;
   }
-  a.hash_slots = std::max(next_pow2(2 * a.ucap), next_pow2(k.threads_per_group));
-  a.hash_bits = log2u(a.hash_slots);
-  a.sort_n = next_pow2(a.max_batch_idx);
-  const uint32_t bytes = frame_slice_bytes(method, (int)shader, a.max_batch_idx, a.ucap, a.hash_slots, a.sort_n,
-                                           k.threads_per_group, 0);
-  if (bytes > kFrameSliceBytes)
+  const uint32_t bytes = frame_capacities(a, method, shader, k.threads_per_group);
+  if (bytes == 0 || bytes > kFrameSliceBytes)
     return fail(c, GP_ERR_UNSUPPORTED,
                 "frame draw " + std::to_string(draw) + ": batch too large for " +
                     std::to_string(k.threads_per_group) + " threads per group");

@@ -115,6 +115,7 @@ int out_floats(int shader);  // K
 enum FrameMethod : int { kFrameNaive = 0, kFrameWarp = 1, kFrameSort = 2, kFrameHash = 3, kFramePHash = 4 };
 constexpr uint32_t kFrameThreads = 256;          // threads per block of the frame kernel
 constexpr uint32_t kFrameSliceBytes = 64 * 1024;  // shared memory for the groups of one block
+constexpr uint32_t kFrameUniBytes = (sizeof(Uniforms) + 127) / 128 * 128;  // the current draw's uniforms
 
 struct FrameDraw {
   DrawArgs a;               // buffers, batching and capacities of the draw (err/counters: the frame's record)
@@ -131,6 +132,9 @@ struct FrameDraw {
 
 uint32_t frame_slice_bytes(int method, int shader, uint32_t max_idx, uint32_t ucap, uint32_t slots, uint32_t sort_n,
                            uint32_t group, uint32_t batch_idx);
+// Shared memory of a sort/hash/phash draw whose group is the whole block
+// (the pipelined path), with the capacities and out_chunk set in 'a'.
+uint32_t frame_pipe_bytes(int method, int shader, const DrawArgs& a);
 size_t frame_smem_bytes();
 int frame_blocks_per_sm();
 // item_draw[i]: the entry of draws[] that work item i belongs to.

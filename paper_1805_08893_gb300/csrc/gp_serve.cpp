@@ -328,9 +328,7 @@ bool launch_step(gp_server* s, StepSlot& st) {
         a.starts = m.part.d_starts;
         D.dynamic = 1;
       }
-      a.hash_slots = std::max(next_pow2(2 * a.ucap), next_pow2(D.group));
-      a.hash_bits = log2u(a.hash_slots);
-      a.sort_n = next_pow2(a.max_batch_idx);
+      frame_capacities(a, (int)D.method, r.shader, D.group);  // checked when the mesh became resident
     } else if (k.variant == GP_WARP) {
       a.static_batch_tris = k.batch_indices / 3;
     }
@@ -544,6 +542,23 @@ gp_status gp_server_create(gp_ctx* c, const gp_serve_config* cfg_in, gp_server**
   if ((k.batch_indices % 3) || (k.variant == GP_WARP && k.batch_indices > 384)) {
     delete s;
     return GP_ERR_INVALID;
+  }
+  if (k.variant >= GP_SORT && k.variant <= GP_PHASH) {  // the groups' shared memory in the frame kernel
+    if (k.threads_per_group != 64 && k.threads_per_group != 128 && k.threads_per_group != kFrameThreads) {
+      delete s;
+      return GP_ERR_INVALID;
+    }
+    const int method = k.variant == GP_SORT ? kFrameSort : (k.variant == GP_HASH ? kFrameHash : kFramePHash);
+    for (uint32_t sh = 0; sh < 4; ++sh) {
+      DrawArgs a{};
+      a.max_batch_idx = k.mode == GP_BATCH_STATIC ? k.batch_indices : 3 * k.max_tris;
+      a.ucap = k.mode == GP_BATCH_STATIC ? k.batch_indices : k.max_unique;
+      const uint32_t need = frame_capacities(a, method, sh, k.threads_per_group);
+      if (need == 0 || need > kFrameSliceBytes) {
+        delete s;
+        return GP_ERR_UNSUPPORTED;
+      }
+    }
   }
   s->k = k;
   cudaSetDevice(c->device);

@@ -41,6 +41,14 @@ FRAME = [
     ("s1", "envelope", "phash", 0, 255, 0, 128),
     ("s2", "load", "sort", 1, 0, 256, 256),
     ("g", "load", "naive", 0, 0, 0, 0),
+    # whole-block groups (the pipelined path) for every method, mode and shader
+    ("s2", "mvp", "phash", 1, 0, 256, 256),
+    ("s2", "mvp", "sort", 0, 510, 0, 256),
+    ("s1", "envelope", "sort", 0, 255, 0, 256),
+    ("g", "envelope", "phash", 1, 0, 128, 256),
+    ("sk", "skin", "phash", 0, 255, 0, 256),
+    ("sk", "skin", "sort", 1, 0, 64, 256),
+    ("s1", "load", "hash", 0, 96, 0, 256),
 ]
 
 
