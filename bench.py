@@ -53,6 +53,9 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--sections", default="heavy,frame,serving,table1,walk,loop",
                     help="extra workloads: heavy, frame, serving, table1, walk, loop (comma list, or 'none')")
+    ap.add_argument("--frame-methods", default="autotuned,naive,hash_dynamic",
+                    help="frame section: configurations to run (autotuned, naive, hash_dynamic); the autotuner and "
+                         "the separate-submission comparison run only with autotuned")
     ap.add_argument("--clock-warm", type=float, default=1.0,
                     help="seconds of headline draws before its warm-up, so the clock sampler sees the GPU under load")
     return ap.parse_args()
@@ -361,12 +364,16 @@ def frame_section(gp, torch, args):
         bufs.append((idx, verts, out, uni))
         descs.append(gp.draw_desc(idx, verts, gp.GP_SHADER_SKIN, uni, out))
     T = int(sum(m.num_tris for m in meshes))
-    t1 = time.time()
-    rng = np.random.default_rng(5)
-    sample = [descs[i] for i in rng.choice(len(descs), size=200, replace=False)]
-    gp.gp_autotune(ctx, sample, reps=3)
-    tune_s = time.time() - t1
-    table = gp.gp_autotune_table(ctx)
+    methods = [m.strip() for m in args.frame_methods.split(",") if m.strip()]
+    tuned = "autotuned" in methods
+    tune_s, table = None, []
+    if tuned:
+        t1 = time.time()
+        rng = np.random.default_rng(5)
+        sample = [descs[i] for i in rng.choice(len(descs), size=200, replace=False)]
+        gp.gp_autotune(ctx, sample, reps=3)
+        tune_s = time.time() - t1
+        table = gp.gp_autotune_table(ctx)
 
     def run(frame):
         for _ in range(args.warmup):
@@ -385,6 +392,8 @@ def frame_section(gp, torch, args):
 
     out = {}
     for name, variant in [("autotuned", gp.GP_AUTO), ("naive", gp.GP_NAIVE), ("hash_dynamic", gp.GP_HASH)]:
+        if name not in methods:
+            continue
         ds = []
         for (idx, verts, o, uni) in bufs:
             ds.append(gp.draw_desc(idx, verts, gp.GP_SHADER_SKIN, uni, o, variant=variant,
@@ -407,6 +416,8 @@ def frame_section(gp, torch, args):
     # the same draws as separate submissions (no fusion), autotuned methods
     ms_sep = None
     try:
+        if not tuned:
+            raise RuntimeError("needs the autotuned configuration")
         ctxs = {}
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         cfgs = []
@@ -440,7 +451,7 @@ def frame_section(gp, torch, args):
         for c in ctxs.values():
             gp.gp_destroy(c)
     except Exception as e:  # reported, not fatal
-        ms_sep = f"failed: {e}"
+        ms_sep = f"failed: {e}" if tuned else "skipped: needs the autotuned configuration"
     gp.gp_destroy(ctx)
     return {"workload": f"{len(meshes)} skinned draws, {T} triangles, one persistent launch per frame",
             "gen_s": gen_s, "autotune_s": tune_s, "autotune_rows": len(table), "frames": out,
