@@ -623,6 +623,9 @@ def serving_section(gp, torch, args):
         algo = sum(12 * pool[i][0].num_tris + pool[i][0].vertices.nbytes + 84 * pool[i][0].num_tris for i in pick)
         res[str(lam)] = {"requests": int(arr.size), "triangles_per_s": tris / (st["wall_ms"] * 1e-3),
                          "hbm_frac": algo / (st["wall_ms"] * 1e-3) / 1e9 / peak,
+                         # the same bytes over the summed device time of the steps (a lower bound of the
+                         # fraction during steps when steps on different streams overlap)
+                         "hbm_frac_busy": algo / (max(st["busy_ms"], 1e-9) * 1e-3) / 1e9 / peak,
                          "offered_triangles_per_s": float(sum(pool[i][0].num_tris for i in pick) / dur),
                          "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
                          "device_busy_frac": st["busy_ms"] / max(st["wall_ms"], 1e-9), "steps": st["steps"]}

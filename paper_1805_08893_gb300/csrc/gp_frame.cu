@@ -242,12 +242,33 @@ __device__ __forceinline__ uint2 frame_pipe_any(const FrameDraw& D, const Unifor
   }
 }
 
-// Work items are handed out in chunks of kFrameChunk consecutive items per
-// atomic, so the counter's latency is paid once per chunk and consecutive
-// items usually belong to the same draw; item_draw[item] names an item's
-// draw, and the draw's descriptor is copied to shared memory only when it
-// changes.
+// Work items are handed out in chunks of consecutive items from a global
+// counter (guided self-scheduling): a chunk is about 1/(4 x blocks) of the
+// items left, at least kFrameChunk and at most kFrameMaxChunk, so long runs
+// of a draw's batches go through the pipeline while much work is left and
+// the last chunks are short.  item_draw[item] names an item's draw, and the
+// draw's descriptor is copied to shared memory only when it changes.
 constexpr uint32_t kFrameChunk = 8;
+constexpr uint32_t kFrameMaxChunk = 64;
+
+// Thread 0: claims the next chunk; returns its first item (>= total when the
+// work is done) and its length in *take.
+__device__ __forceinline__ uint32_t claim_chunk(uint32_t* work, uint32_t total, uint32_t* take) {
+  volatile uint32_t* vw = work;
+  uint32_t base = *vw;
+  for (uint32_t tries = 0; base < total; ++tries) {
+    const uint32_t t = min(kFrameMaxChunk, max(kFrameChunk, (total - base) / (4u * gridDim.x)));
+    if (tries == 64) break;  // heavy contention: take a fixed chunk instead
+    const uint32_t prev = atomicCAS(work, base, base + t);
+    if (prev == base) {
+      *take = t;
+      return base;
+    }
+    base = prev;
+  }
+  *take = kFrameChunk;
+  return base < total ? atomicAdd(work, kFrameChunk) : base;
+}
 
 __global__ void __launch_bounds__(kFrameThreads, 3) frame_kernel(const FrameDraw* __restrict__ draws,
                                                                  const uint32_t* __restrict__ item_draw,
@@ -256,7 +277,7 @@ __global__ void __launch_bounds__(kFrameThreads, 3) frame_kernel(const FrameDraw
   extern __shared__ __align__(128) unsigned char smem[];
   Uniforms* su = reinterpret_cast<Uniforms*>(smem);  // the current draw's uniforms (and palette)
   unsigned char* slices = smem + kFrameUniBytes;
-  __shared__ uint32_t s_base;
+  __shared__ uint32_t s_base, s_take;
   __shared__ __align__(16) FrameDraw s_draw;  // the current item's draw, read from shared memory
   __shared__ __align__(8) uint64_t s_bars[2];  // index-window mbarriers of the pipelined path
   if (threadIdx.x == 0) {
@@ -269,11 +290,11 @@ __global__ void __launch_bounds__(kFrameThreads, 3) frame_kernel(const FrameDraw
   uint32_t cur_draw = 0xFFFFFFFFu;
   bool aborted = false;
   while (!aborted) {
-    if (threadIdx.x == 0) s_base = atomicAdd(work, kFrameChunk);
+    if (threadIdx.x == 0) s_base = claim_chunk(work, total_items, &s_take);
     __syncthreads();
     const uint32_t base = s_base;
     if (base >= total_items) break;
-    const uint32_t end = min(base + kFrameChunk, total_items);
+    const uint32_t end = min(base + s_take, total_items);
     for (uint32_t item = base; item < end;) {
       const uint32_t d = __ldg(item_draw + item);  // uniform across the block
       if (d != cur_draw) {
