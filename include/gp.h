@@ -364,6 +364,7 @@ typedef struct gp_serve_stats {
   double wall_ms;                /* first submission to last completion */
   uint32_t last_error;           /* gp_status of the last failed step, or GP_OK */
   uint32_t pad;
+  double device_ms;              /* union of the steps' device intervals: time with >= 1 step in flight */
 } gp_serve_stats;
 
 /* Starts a server (and its thread) on the context's device.  The context

@@ -117,7 +117,8 @@ class gp_serve_stats(ctypes.Structure):
                 ("invocations", ctypes.c_uint64), ("steps", ctypes.c_uint64), ("uploads", ctypes.c_uint64),
                 ("evictions", ctypes.c_uint64), ("resident_bytes", ctypes.c_uint64), ("p50_ms", ctypes.c_double),
                 ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double), ("busy_ms", ctypes.c_double),
-                ("wall_ms", ctypes.c_double), ("last_error", ctypes.c_uint32), ("pad", ctypes.c_uint32)]
+                ("wall_ms", ctypes.c_double), ("last_error", ctypes.c_uint32), ("pad", ctypes.c_uint32),
+                ("device_ms", ctypes.c_double)]
 
 
 class gp_walk_desc(ctypes.Structure):

@@ -118,6 +118,12 @@ struct gp_server {
   std::vector<double> lat;
   uint64_t s_tris = 0, s_inv = 0, s_steps = 0, s_uploads = 0, s_evictions = 0;
   double s_busy = 0.0;
+  // device time of the steps as intervals against a reference event recorded
+  // before the first step of the statistics window (their union is the time
+  // the device had at least one step in flight)
+  cudaEvent_t ev_ref = nullptr;
+  bool ref_set = false;
+  std::vector<std::pair<float, float>> step_iv;
   bool have_first = false;
   Clock::time_point first_submit, last_done;
   gp_status last_error = GP_OK;
@@ -364,6 +370,10 @@ bool launch_step(gp_server* s, StepSlot& st) {
     h_draws[i].a.err = &d_rec->err;
   }
   cudaStream_t q = st.stream;
+  if (!s->ref_set) {
+    cudaEventRecord(s->ev_ref, q);
+    s->ref_set = true;
+  }
   cudaEventRecord(st.ev0, q);
   cudaMemcpyAsync(st.d_block, st.h_block, bytes, cudaMemcpyHostToDevice, q);
   const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)s->ctx->sms * s->frame_bpsm, items));
@@ -383,6 +393,10 @@ void complete_step(gp_server* s, StepSlot& st) {
   float ms = 0.f;
   cudaEventElapsedTime(&ms, st.ev0, st.ev1);
   s->s_busy += ms;
+  float a = 0.f, b = 0.f;
+  if (cudaEventElapsedTime(&a, s->ev_ref, st.ev0) == cudaSuccess &&
+      cudaEventElapsedTime(&b, s->ev_ref, st.ev1) == cudaSuccess)
+    s->step_iv.push_back({a, b});
   s->s_inv += st.h_rec->cnt[CNT_INVOCATIONS];
   gp_status err = GP_OK;
   if (st.h_rec->err & EBIT_INDEX_RANGE) err = GP_ERR_INDEX_RANGE;
@@ -435,6 +449,7 @@ void server_loop(gp_server* s) {
 }
 
 void free_server(gp_server* s) {
+  if (s->ev_ref) cudaEventDestroy(s->ev_ref);
   for (StepSlot& st : s->steps) {
     if (st.stream) cudaStreamDestroy(st.stream);
     if (st.ev0) cudaEventDestroy(st.ev0);
@@ -563,6 +578,7 @@ gp_status gp_server_create(gp_ctx* c, const gp_serve_config* cfg_in, gp_server**
   s->k = k;
   cudaSetDevice(c->device);
   cudaError_t e = cudaStreamCreateWithFlags(&s->upload, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&s->ev_ref);
   s->steps.resize(cfg.streams);
   for (StepSlot& st : s->steps) {
     if (e != cudaSuccess) break;
@@ -684,6 +700,24 @@ gp_status gp_server_stats(gp_server* s, gp_serve_stats* out, int reset) {
   out->evictions = s->s_evictions;
   out->resident_bytes = s->resident_bytes;
   out->busy_ms = s->s_busy;
+  {  // union of the step intervals
+    std::vector<std::pair<float, float>> iv = s->step_iv;
+    std::sort(iv.begin(), iv.end());
+    double total = 0.0, lo = 0.0, hi = 0.0;
+    bool open = false;
+    for (const auto& x : iv) {
+      if (open && x.first <= hi) {
+        hi = std::max<double>(hi, x.second);
+      } else {
+        if (open) total += hi - lo;
+        lo = x.first;
+        hi = x.second;
+        open = true;
+      }
+    }
+    if (open) total += hi - lo;
+    out->device_ms = total;
+  }
   out->last_error = (uint32_t)s->last_error;
   if (s->have_first && s->completed) out->wall_ms = ms_between(s->first_submit, s->last_done);
   if (!s->lat.empty()) {
@@ -698,6 +732,8 @@ gp_status gp_server_stats(gp_server* s, gp_serve_stats* out, int reset) {
     s->lat.clear();
     s->s_tris = s->s_inv = s->s_steps = s->s_uploads = s->s_evictions = 0;
     s->s_busy = 0.0;
+    s->step_iv.clear();
+    s->ref_set = false;
     s->have_first = false;
     s->last_error = GP_OK;
     // forget finished requests (their ids stay unique)

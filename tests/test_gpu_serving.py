@@ -72,6 +72,10 @@ def test_mix_invariance(variant, mode):
             assert st["completed"] == n and st["submitted"] == n
             assert st["p99_ms"] >= st["p50_ms"] > 0 and st["steps"] >= 1
             assert st["triangles"] == sum(r[0].num_tris for r in reqs)
+            # device time: the union of the step intervals is at most their sum and the wall time
+            # (up to the rounding of float event timestamps, ~0.5 us each)
+            assert 0 < st["device_ms"] <= st["busy_ms"] * 1.001 + 1e-3 * st["steps"]
+            assert st["device_ms"] <= st["wall_ms"] * 1.001 + 1e-3 * st["steps"]
             for i in (0, 1, 2, 5, n // 2, n - 1):
                 mesh, mid, sid, uni, uni_o, out = reqs[i]
                 got = out.cpu().numpy()
