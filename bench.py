@@ -183,14 +183,17 @@ sys.path.insert(0, {root!r})
 import numpy as np
 import meshgen as mg
 from oracle import shading as S
-mesh = mg.geodesic_sphere({freq}, {seed})
+if {vpath!r}:
+    mesh = mg.Mesh(np.load({vpath!r}), np.load({ipath!r}))
+else:
+    mesh = mg.geodesic_sphere({freq}, {seed})
 M, N = mg.mvp_uniforms({cam})
 uni = {{"M": M, "N": N}}
 T = mesh.num_tris
 chunk = {chunk}
 budget = {budget}
 done = 0
-rng = np.random.default_rng(0)
+rng = np.random.default_rng({rng_seed})
 t0 = time.perf_counter()
 times = []
 while True:
@@ -206,16 +209,48 @@ print(json.dumps({{"tris": done, "seconds": el, "steps": len(times), "per_step":
 """
 
 
-def run_oracle(freq, chunk, budget, min_steps=1):
+def _oracle_env():
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[v] = "1"
+    return env
+
+
+def run_oracle(freq, chunk, budget, min_steps=1):
+    """The oracle in a fresh single-threaded process on samples of the mesh."""
     code = CPU_SNIPPET.format(root=ROOT, freq=freq, seed=MESH_SEED, cam=CAM_SEED, chunk=chunk, budget=budget,
-                              min_steps=min_steps)
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+                              min_steps=min_steps, vpath="", ipath="", rng_seed=0)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=_oracle_env())
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_oracle_parallel(mesh, chunk, budget, procs):
+    """The oracle in 'procs' fresh single-threaded processes at once (one per
+    host core), each on its own seeded samples of the same mesh, which they
+    load from files.  Returns (triangles/s summed over the processes,
+    triangles, processes)."""
+    import tempfile
+    with tempfile.TemporaryDirectory() as tmp:
+        vpath, ipath = os.path.join(tmp, "v.npy"), os.path.join(tmp, "i.npy")
+        np.save(vpath, mesh.vertices)
+        np.save(ipath, mesh.indices)
+        ps = []
+        for i in range(procs):
+            code = CPU_SNIPPET.format(root=ROOT, freq=0, seed=0, cam=CAM_SEED, chunk=chunk, budget=budget,
+                                      min_steps=1, vpath=vpath, ipath=ipath, rng_seed=1 + i)
+            ps.append(subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
+                                       stderr=subprocess.PIPE, text=True, env=_oracle_env()))
+        rate, tris = 0.0, 0
+        for p in ps:
+            out, err = p.communicate()
+            if p.returncode != 0:
+                raise RuntimeError(err[-2000:])
+            res = json.loads(out.strip().splitlines()[-1])
+            rate += res["tris"] / res["seconds"]
+            tris += res["tris"]
+    return rate, tris, procs
 
 
 def headline_config(f, world):
@@ -807,6 +842,14 @@ def main():
         cpu = {"value": res["tris"] / res["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{res['steps']} x {chunk} consecutive triangles of the benchmark mesh at seeded "
                          f"offsets, float64 numpy oracle (plain definition), one thread"}
+        try:  # the same oracle on every host core at once: one process per core
+            procs = os.cpu_count() or 1
+            rate, tris, procs = run_oracle_parallel(mesh, chunk, 8.0, procs)
+            cpu["all_cores"] = {"value": rate, "unit": UNIT, "cores": procs,
+                                "sample": f"{procs} processes, each {chunk}-triangle samples at its own seeded "
+                                          f"offsets for ~8 s ({tris} triangles in all)"}
+        except Exception as e:  # reported, not fatal
+            cpu["all_cores"] = f"failed: {e}"
 
     if rank == 0:
         line = {
