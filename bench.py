@@ -636,10 +636,11 @@ def serving_section(gp, torch, args):
     outs = [torch.empty(m.num_tris * 21, dtype=torch.float32, device="cuda") for m, _ in pool]
     peak, peak_kind = load_peaks()
     runs = {}
-    # 3 streams: a step starts whenever a stream is free; 1 stream: requests that
-    # arrive during a step wait for the next one, so steps are larger
-    for streams, key in ((3, "rates"), (1, "rates_1stream")):
-        srv = gp.gp_server_create(ctx, mem_budget_bytes=20 << 30, streams=streams, step_max_batches=2048)
+    # the server's defaults (3 streams, steps of up to 32,768 batches); steps of
+    # at most 2,048 batches (many small steps under load); 1 stream (requests
+    # that arrive during a step wait for the next one)
+    for streams, smax, key in ((3, 32768, "rates"), (3, 2048, "rates_2k_steps"), (1, 32768, "rates_1stream")):
+        srv = gp.gp_server_create(ctx, mem_budget_bytes=20 << 30, streams=streams, step_max_batches=smax)
         mids = [gp.gp_server_add_mesh(srv, m.indices, m.vertices) for m, _ in pool]
         # warm: every mesh resident once
         for k in range(len(pool)):
@@ -648,7 +649,7 @@ def serving_section(gp, torch, args):
         gp.gp_server_wait(srv)
         gp.gp_server_stats(srv, reset=True)
         res = {}
-        for lam in (5000, 10000, 20000, 50000, 100000, 200000, 500000):
+        for lam in (5000, 10000, 20000, 50000, 100000, 200000, 500000) + ((1000000,) if key == "rates" else ()):
             dur = 1.0 if lam <= 50000 else 0.25
             arr = mg.poisson_arrivals(lam, lam, dur)
             pick = rng.integers(0, len(pool), size=arr.size)

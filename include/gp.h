@@ -345,7 +345,7 @@ typedef struct gp_server gp_server;
 typedef struct gp_serve_config {
   uint64_t mem_budget_bytes;  /* device bytes for resident meshes [20 GiB] */
   uint32_t streams;           /* steps in flight at once [2] */
-  uint32_t step_max_batches;  /* batches per step [2048] */
+  uint32_t step_max_batches;  /* batches per step [32768]: small steps under load leave the device underused */
   uint32_t max_active;        /* requests admitted at once [4096] */
   int32_t variant;            /* method for every request: GP_NAIVE..GP_PHASH or GP_AUTO [GP_HASH] */
   int32_t mode;               /* gp_batch_mode (sort/hash/phash) [GP_BATCH_DYNAMIC] */

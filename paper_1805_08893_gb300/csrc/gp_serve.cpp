@@ -523,7 +523,7 @@ gp_status gp_server_create(gp_ctx* c, const gp_serve_config* cfg_in, gp_server**
   gp_serve_config& cfg = s->cfg;
   if (!cfg.mem_budget_bytes) cfg.mem_budget_bytes = 20ull << 30;
   if (!cfg.streams) cfg.streams = 2;
-  if (!cfg.step_max_batches) cfg.step_max_batches = 2048;
+  if (!cfg.step_max_batches) cfg.step_max_batches = 32768;
   if (!cfg.max_active) cfg.max_active = 4096;
   if (!cfg_in) {
     cfg.variant = GP_HASH;
