@@ -321,7 +321,7 @@ gp_status check_index_buf(gp_ctx* c, const gp_index_buf* ib) {
 
 // Enqueues one draw (after validation); fills the ticket's counters.
 gp_status enqueue_draw(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* vb, uint32_t shader,
-                       const Uniforms& u, const gp_out_buf* ob, Ticket& t, DevRec* rec) {
+                       const Uniforms& u, const gp_out_buf* ob, Ticket& t, DevRec* rec, Partition* pre) {
   const gp_config& cfg = c->cfg;
   const uint32_t T = (uint32_t)(ib->num_indices / 3);
   DrawArgs a{};
@@ -390,7 +390,10 @@ gp_status enqueue_draw(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* v
   const bool dyn = cfg.mode == GP_BATCH_DYNAMIC;
   if (dyn) {
     Partition* p = nullptr;
-    if (ib->partition) {
+    if (pre) {  // gp_draw_host: the chunk's partition, on its own stream
+      p = pre;
+      GP_CUDA(c, cudaStreamWaitEvent(c->stream, p->done, 0));
+    } else if (ib->partition) {
       auto it = c->parts.find(ib->partition);
       if (it == c->parts.end()) return fail(c, GP_ERR_INVALID, "unknown partition handle");
       p = &it->second;
@@ -527,7 +530,8 @@ gp_status new_ticket(gp_ctx* c, Ticket& t) {
 }
 
 gp_status submit_locked(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* vb, uint32_t shader,
-                        const void* uniforms, uint32_t ubytes, const gp_out_buf* ob, uint64_t* out_ticket) {
+                        const void* uniforms, uint32_t ubytes, const gp_out_buf* ob, uint64_t* out_ticket,
+                        Partition* pre) {
   gp_status s = check_draw(c, ib, vb, shader, ob);
   if (s != GP_OK) return s;
   Uniforms u;
@@ -539,7 +543,7 @@ gp_status submit_locked(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* 
   DevRec* rec = c->d_rec + t.slot;
   GP_CUDA(c, cudaEventRecord(t.ev0, c->stream));
   GP_CUDA(c, cudaMemsetAsync(rec, 0, sizeof(DevRec), c->stream));
-  s = enqueue_draw(c, ib, vb, shader, u, ob, t, rec);
+  s = enqueue_draw(c, ib, vb, shader, u, ob, t, rec, pre);
   if (s != GP_OK) {
     put_event(c, t.ev0);
     put_event(c, t.ev1);
@@ -641,6 +645,7 @@ gp_status gp_destroy(gp_ctx* c) {
     c->inflight.clear();
     for (auto& kv : c->parts) release_partition(kv.second);
     release_partition(c->temp_part);
+    for (Partition& p : c->host_parts) release_partition(p);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     if (c->d_rec) cudaFree(c->d_rec);
     if (c->h_rec) cudaFreeHost(c->h_rec);
@@ -650,6 +655,7 @@ gp_status gp_destroy(gp_ctx* c) {
     if (c->d_shaded) cudaFree(c->d_shaded);
     if (c->copy_in) cudaStreamDestroy(c->copy_in);
     if (c->copy_out) cudaStreamDestroy(c->copy_out);
+    if (c->part_stream) cudaStreamDestroy(c->part_stream);
     if (c->aux) cudaStreamDestroy(c->aux);
   }
   delete c;
@@ -735,7 +741,7 @@ gp_status gp_submit_drawcall(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_
   if (!c) return GP_ERR_INVALID;
   std::lock_guard<std::mutex> lk(c->mu);
   cudaSetDevice(c->device);
-  return submit_locked(c, ib, vb, shader_id, uniforms, uniforms_bytes, out_tris, out_ticket);
+  return submit_locked(c, ib, vb, shader_id, uniforms, uniforms_bytes, out_tris, out_ticket, nullptr);
 }
 
 gp_status gp_sync(gp_ctx* c, uint64_t ticket, uint32_t timeout_ms) {
@@ -814,6 +820,17 @@ gp_status gp_draw_host(gp_ctx* c, const uint32_t* indices_host, uint64_t num_ind
   if (granule) chunk = std::max<uint64_t>(1, (kHostChunkTris + granule / 2) / granule) * granule;
   if (chunk == 0) chunk = 1;
 
+  // dynamic batches: one partition per chunk on its own stream, started as
+  // soon as the chunk's indices have arrived; the first chunk's indices go up
+  // before the vertices, so its partition overlaps the vertex upload
+  const bool pre_part = cfg.mode == GP_BATCH_DYNAMIC && cfg.variant >= GP_SORT && cfg.variant <= GP_PHASH &&
+                        granule && T > 0;
+  const uint64_t nchunks = T ? (T + chunk - 1) / chunk : 1;
+  if (pre_part) {
+    if (!c->part_stream) GP_CUDA(c, cudaStreamCreateWithFlags(&c->part_stream, cudaStreamNonBlocking));
+    if (c->host_parts.size() < nchunks) c->host_parts.resize(nchunks);
+  }
+
   std::vector<cudaEvent_t> evs;
   auto new_event = [&]() {
     cudaEvent_t e = get_event(c);
@@ -822,11 +839,32 @@ gp_status gp_draw_host(gp_ctx* c, const uint32_t* indices_host, uint64_t num_ind
   };
   auto finish = [&](gp_status st) {
     cudaStreamSynchronize(c->copy_in);
+    if (c->part_stream) cudaStreamSynchronize(c->part_stream);
     cudaStreamSynchronize(c->stream);
     cudaStreamSynchronize(c->copy_out);
     for (cudaEvent_t e : evs) put_event(c, e);
     return st;
   };
+  std::vector<cudaEvent_t> ev_in(nchunks, nullptr);
+  auto upload_indices = [&](uint64_t k) -> gp_status {
+    const uint64_t t0 = k * chunk, nt = T ? std::min<uint64_t>(chunk, T - t0) : 0;
+    uint32_t* d_idx = static_cast<uint32_t*>(c->h_idx) + 3 * t0;
+    if (!(ev_in[k] = new_event())) return fail(c, GP_ERR_CUDA, "cudaEventCreate failed");
+    if (nt) GP_CUDA(c, cudaMemcpyAsync(d_idx, indices_host + 3 * t0, nt * 12, cudaMemcpyHostToDevice, c->copy_in));
+    GP_CUDA(c, cudaEventRecord(ev_in[k], c->copy_in));
+    if (pre_part) {
+      Partition& p = c->host_parts[k];
+      gp_status st = size_partition(c, p, 3 * nt, true, cfg.max_unique, cfg.max_tris, cfg.segment_tris);
+      if (st != GP_OK) return st;
+      p.idx = d_idx;
+      if (!p.done) GP_CUDA(c, cudaEventCreateWithFlags(&p.done, cudaEventDisableTiming));
+      GP_CUDA(c, cudaStreamWaitEvent(c->part_stream, ev_in[k], 0));
+      if ((st = run_partition(c, p, d_idx, 3 * nt, c->part_stream)) != GP_OK) return st;
+      GP_CUDA(c, cudaEventRecord(p.done, c->part_stream));
+    }
+    return GP_OK;
+  };
+  if (pre_part && (s = upload_indices(0)) != GP_OK) return finish(s);
   cudaEvent_t ev_v = new_event();
   if (!ev_v) return finish(fail(c, GP_ERR_CUDA, "cudaEventCreate failed"));
   if (num_vertices)
@@ -834,25 +872,25 @@ gp_status gp_draw_host(gp_ctx* c, const uint32_t* indices_host, uint64_t num_ind
                                c->copy_in));
   GP_CUDA(c, cudaEventRecord(ev_v, c->copy_in));
   GP_CUDA(c, cudaStreamWaitEvent(c->stream, ev_v, 0));
+  for (uint64_t k = pre_part ? 1 : 0; k < nchunks; ++k)
+    if ((s = upload_indices(k)) != GP_OK) return finish(s);
   uint64_t ticket = 0;
   gp_vertex_buf vb{c->h_vtx, num_vertices, stride_bytes, format};
-  for (uint64_t t0 = 0; t0 < T || (T == 0 && t0 == 0); t0 += chunk) {
-    const uint64_t nt = std::min<uint64_t>(chunk, T - t0);
+  for (uint64_t k = 0; k < nchunks; ++k) {
+    const uint64_t t0 = k * chunk, nt = T ? std::min<uint64_t>(chunk, T - t0) : 0;
     uint32_t* d_idx = static_cast<uint32_t*>(c->h_idx) + 3 * t0;
     float* d_out = static_cast<float*>(c->h_out) + 3 * K * t0;
-    cudaEvent_t ev_in = new_event(), ev_done = new_event();
-    if (!ev_in || !ev_done) return finish(fail(c, GP_ERR_CUDA, "cudaEventCreate failed"));
-    if (nt) GP_CUDA(c, cudaMemcpyAsync(d_idx, indices_host + 3 * t0, nt * 12, cudaMemcpyHostToDevice, c->copy_in));
-    GP_CUDA(c, cudaEventRecord(ev_in, c->copy_in));
-    GP_CUDA(c, cudaStreamWaitEvent(c->stream, ev_in, 0));
+    cudaEvent_t ev_done = new_event();
+    if (!ev_done) return finish(fail(c, GP_ERR_CUDA, "cudaEventCreate failed"));
+    GP_CUDA(c, cudaStreamWaitEvent(c->stream, ev_in[k], 0));
     gp_index_buf ib{d_idx, 3 * nt, 0};
     gp_out_buf ob{d_out, nt * 3 * K * 4, nullptr, nullptr, 0};
-    s = submit_locked(c, &ib, &vb, shader_id, uniforms, uniforms_bytes, &ob, &ticket);
+    s = submit_locked(c, &ib, &vb, shader_id, uniforms, uniforms_bytes, &ob, &ticket,
+                      pre_part ? &c->host_parts[k] : nullptr);
     if (s != GP_OK) return finish(s);
     GP_CUDA(c, cudaEventRecord(ev_done, c->stream));
     GP_CUDA(c, cudaStreamWaitEvent(c->copy_out, ev_done, 0));
     if (nt) GP_CUDA(c, cudaMemcpyAsync(out_host + 3 * K * t0, d_out, nt * 3 * K * 4, cudaMemcpyDeviceToHost, c->copy_out));
-    if (T == 0) break;
   }
   s = finish(GP_OK);
   return sync_locked(c, ticket, 0);

@@ -104,8 +104,10 @@ struct gp_ctx {
   // autotune table (frame draws with GP_AUTO), see gp_frame_api.cpp
   std::vector<gp_autotune_entry> tune;
   // gp_draw_host: copy streams (created on first use), so that uploads, draws
-  // and read-backs of consecutive chunks overlap
-  cudaStream_t copy_in = nullptr, copy_out = nullptr;
+  // and read-backs of consecutive chunks overlap; dynamic batches: one
+  // partition per chunk, run on their own stream as the chunk's indices arrive
+  cudaStream_t copy_in = nullptr, copy_out = nullptr, part_stream = nullptr;
+  std::vector<gp::rt::Partition> host_parts;
   // GP_MULTI: shaded vertex rows (32 B each), grown to the largest vertex buffer drawn
   float4* d_shaded = nullptr;
   size_t shaded_cap = 0;  // vertices
