@@ -51,8 +51,8 @@ def parse_args():
     ap.add_argument("--frequency", type=int, default=FREQ, help="geodesic frequency (600 = the benchmark mesh)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--sections", default="heavy,frame,serving,table1,walk,loop",
-                    help="extra workloads: heavy, frame, serving, table1, walk, loop (comma list, or 'none')")
+    ap.add_argument("--sections", default="heavy,table2,frame,serving,table1,walk,loop",
+                    help="extra workloads: heavy, table2, frame, serving, table1, walk, loop (comma list, or 'none')")
     ap.add_argument("--frame-methods", default="autotuned,naive,hash_dynamic",
                     help="frame section: configurations to run (autotuned, naive, hash_dynamic); the autotuner and "
                          "the separate-submission comparison run only with autotuned")
@@ -372,6 +372,47 @@ def heavy_section(gp, torch, args):
             "best": best, "best_vs_naive": res[best]["vs_naive"],
             "naive_fp32_frac": res["naive"]["gflops_algorithmic"] / 1e3 / peak,
             "variants": res}
+
+
+def table2_section(gp, torch, args):
+    """Table 2's shader rows on the dragon-sized mesh (the benchmark mesh):
+    the simple MVP shader and the shader with a load of N cycles, read as a
+    dependent FMA chain of N/4 steps, for N = 256, 512 and 1024 as in the
+    paper and 4096 and 16384 beyond it; every method of the table."""
+    mesh = mg.geodesic_sphere(args.frequency, MESH_SEED)
+    T, V = mesh.num_tris, mesh.num_vertices
+    M, N = mg.mvp_uniforms(CAM_SEED)
+    idx = torch.from_numpy(mesh.indices.view(np.int32)).cuda()
+    verts = torch.from_numpy(mesh.vertices).cuda()
+    out = torch.empty(T * 21, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    methods = [("naive", "naive", 0, {}), ("warp", "warp", 0, {"batch_indices": 96}), ("hash", "hash", 1, {}),
+               ("phash", "phash", 1, {}), ("sort", "sort", 1, {}), ("multi", "multi", 0, {})]
+    ctxs = []
+    for name, variant, mode, extra in methods:
+        ctx = gp.gp_create(variant, mode=mode, stream=stream, **extra)
+        handle = gp.gp_partition(ctx, idx)[0] if mode == 1 else 0
+        ctxs.append((name, ctx, handle))
+    rows = {}
+    steps = max(1, min(args.steps, 20))
+    for cycles in (0, 256, 512, 1024, 4096, 16384):
+        sid = gp.GP_SHADER_MVP if cycles == 0 else gp.GP_SHADER_LOAD
+        uni = gp.uniforms_mvp(M, N) if cycles == 0 else gp.uniforms_load(M, N, cycles // 4)
+        row = {}
+        for name, ctx, handle in ctxs:
+            ms, st = time_draws(gp, torch, ctx, idx, verts, sid, uni, out, handle, steps, args.warmup)
+            row[name] = {"ms": ms, "shading_rate": st["invocations"] / max(1, st["draws"]) / V}
+        for v in row.values():
+            v["vs_naive"] = row["naive"]["ms"] / v["ms"]
+        best = min(row, key=lambda k: row[k]["ms"])
+        rows["simple" if cycles == 0 else f"{cycles} cycles"] = {"methods": row, "best": best,
+                                                                 "best_vs_naive": row[best]["vs_naive"]}
+    for _, ctx, handle in ctxs:
+        if handle:
+            gp.gp_partition_release(ctx, handle)
+        gp.gp_destroy(ctx)
+    return {"workload": f"geodesic sphere f={args.frequency} ({V} vertices / {T} triangles); load shader: "
+                        "N cycles = a dependent chain of N/4 FMAs per shaded vertex", "rows": rows}
 
 
 def frame_section(gp, torch, args):
@@ -885,7 +926,8 @@ def main():
             del idx, verts, out
             torch.cuda.empty_cache()
             extra = {}
-            for name, fn in (("heavy", heavy_section), ("frame", frame_section), ("serving", serving_section),
+            for name, fn in (("heavy", heavy_section), ("table2", table2_section), ("frame", frame_section),
+                             ("serving", serving_section),
                              ("table1", table1_section), ("walk", walk_section), ("loop", loop_section)):
                 if name in sections:
                     t0 = time.time()
