@@ -119,11 +119,14 @@ struct gp_server {
   uint64_t s_tris = 0, s_inv = 0, s_steps = 0, s_uploads = 0, s_evictions = 0;
   double s_busy = 0.0;
   // device time of the steps as intervals against a reference event recorded
-  // before the first step of the statistics window (their union is the time
-  // the device had at least one step in flight)
+  // before the first step after the last idle point (their union is the time
+  // the device had at least one step in flight); dev_folded holds the union
+  // of the intervals folded away (at idle points, or the oldest ones when
+  // many accumulate under continuous load)
   cudaEvent_t ev_ref = nullptr;
   bool ref_set = false;
   std::vector<std::pair<float, float>> step_iv;
+  double dev_folded = 0.0;
   bool have_first = false;
   Clock::time_point first_submit, last_done;
   gp_status last_error = GP_OK;
@@ -388,6 +391,50 @@ bool launch_step(gp_server* s, StepSlot& st) {
   return true;
 }
 
+// Total length of the union of intervals (sorts them).
+double union_ms(std::vector<std::pair<float, float>>& iv) {
+  std::sort(iv.begin(), iv.end());
+  double total = 0.0, lo = 0.0, hi = 0.0;
+  bool open = false;
+  for (const auto& x : iv) {
+    if (open && x.first <= hi) {
+      hi = std::max<double>(hi, x.second);
+    } else {
+      if (open) total += hi - lo;
+      lo = x.first;
+      hi = x.second;
+      open = true;
+    }
+  }
+  if (open) total += hi - lo;
+  return total;
+}
+
+// Keeps the interval list short.  With no step in flight every interval is
+// folded into dev_folded and the next step records a new reference event
+// (so the timestamps stay small and precise).  Under continuous load, once
+// kMaxIntervals accumulate, the merged intervals that end before the start of
+// the 1024 latest ones are folded: a step still in flight (at most one per
+// stream) overlaps only recent ones.  Called with s->mu held.
+constexpr size_t kMaxIntervals = 1u << 16;
+void fold_intervals(gp_server* s, bool idle) {
+  auto& iv = s->step_iv;
+  if (iv.empty()) return;
+  if (idle) {
+    s->dev_folded += union_ms(iv);
+    iv.clear();
+    s->ref_set = false;
+    return;
+  }
+  if (iv.size() < kMaxIntervals) return;
+  std::sort(iv.begin(), iv.end());
+  const float keep_from = iv[iv.size() - 1024].first;
+  std::vector<std::pair<float, float>> kept, old;
+  for (const auto& x : iv) (x.second < keep_from ? old : kept).push_back(x);
+  s->dev_folded += union_ms(old);
+  iv.swap(kept);
+}
+
 // Folds a completed step.  Called with s->mu held.
 void complete_step(gp_server* s, StepSlot& st) {
   float ms = 0.f;
@@ -429,6 +476,11 @@ void server_loop(gp_server* s) {
         complete_step(s, st);
         progressed = true;
       }
+    }
+    {
+      bool in_flight = false;
+      for (StepSlot& st : s->steps) in_flight |= st.busy;
+      fold_intervals(s, !in_flight);
     }
     if (progressed) s->cv_done.notify_all();
     admit(s);
@@ -702,21 +754,7 @@ gp_status gp_server_stats(gp_server* s, gp_serve_stats* out, int reset) {
   out->busy_ms = s->s_busy;
   {  // union of the step intervals
     std::vector<std::pair<float, float>> iv = s->step_iv;
-    std::sort(iv.begin(), iv.end());
-    double total = 0.0, lo = 0.0, hi = 0.0;
-    bool open = false;
-    for (const auto& x : iv) {
-      if (open && x.first <= hi) {
-        hi = std::max<double>(hi, x.second);
-      } else {
-        if (open) total += hi - lo;
-        lo = x.first;
-        hi = x.second;
-        open = true;
-      }
-    }
-    if (open) total += hi - lo;
-    out->device_ms = total;
+    out->device_ms = s->dev_folded + union_ms(iv);
   }
   out->last_error = (uint32_t)s->last_error;
   if (s->have_first && s->completed) out->wall_ms = ms_between(s->first_submit, s->last_done);
@@ -733,6 +771,7 @@ gp_status gp_server_stats(gp_server* s, gp_serve_stats* out, int reset) {
     s->s_tris = s->s_inv = s->s_steps = s->s_uploads = s->s_evictions = 0;
     s->s_busy = 0.0;
     s->step_iv.clear();
+    s->dev_folded = 0.0;
     s->ref_set = false;
     s->have_first = false;
     s->last_error = GP_OK;
