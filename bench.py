@@ -56,6 +56,8 @@ def parse_args():
     ap.add_argument("--frame-methods", default="autotuned,naive,hash_dynamic",
                     help="frame section: configurations to run (autotuned, naive, hash_dynamic); the autotuner and "
                          "the separate-submission comparison run only with autotuned")
+    ap.add_argument("--frame-nearest-bones", type=int, default=1,
+                    help="frame section: also run the frame with spatially coherent bone ids (1) or not (0)")
     ap.add_argument("--clock-warm", type=float, default=1.0,
                     help="seconds of headline draws before its warm-up, so the clock sampler sees the GPU under load")
     return ap.parse_args()
@@ -422,23 +424,26 @@ def frame_section(gp, torch, args):
     chosen per mesh by the autotuner."""
     t0 = time.time()
     sizes = mg.frame_sizes()
-    meshes, pals = [], []
-    for k, n in enumerate(sizes):
-        m, pal = mg.skin_mesh(mg.frame_mesh(k, int(n)), k)
-        meshes.append(m)
-        pals.append(pal)
+    base = [mg.frame_mesh(k, int(n)) for k, n in enumerate(sizes)]
     gen_s = time.time() - t0
     stream = torch.cuda.current_stream()
     ctx = gp.gp_create("hash", stream=stream)
-    bufs, descs = [], []
-    for k, (m, pal) in enumerate(zip(meshes, pals)):
-        M, N = mg.mvp_uniforms(1000 + k)
-        uni = gp.uniforms_skin(M, N, pal)
-        idx = torch.from_numpy(m.indices.view(np.int32)).cuda()
-        verts = torch.from_numpy(m.vertices).cuda()
-        out = torch.empty(m.num_tris * 21, dtype=torch.float32, device="cuda")
-        bufs.append((idx, verts, out, uni))
-        descs.append(gp.draw_desc(idx, verts, gp.GP_SHADER_SKIN, uni, out))
+
+    def build(bones):
+        meshes, bufs, descs = [], [], []
+        for k, g in enumerate(base):
+            m, pal = mg.skin_mesh(g, k, bones=bones)
+            M, N = mg.mvp_uniforms(1000 + k)
+            uni = gp.uniforms_skin(M, N, pal)
+            idx = torch.from_numpy(m.indices.view(np.int32)).cuda()
+            verts = torch.from_numpy(m.vertices).cuda()
+            out = torch.empty(m.num_tris * 21, dtype=torch.float32, device="cuda")
+            meshes.append(m)
+            bufs.append((idx, verts, out, uni))
+            descs.append(gp.draw_desc(idx, verts, gp.GP_SHADER_SKIN, uni, out))
+        return meshes, bufs, descs
+
+    meshes, bufs, descs = build("uniform")
     T = int(sum(m.num_tris for m in meshes))
     methods = [m.strip() for m in args.frame_methods.split(",") if m.strip()]
     tuned = "autotuned" in methods
@@ -466,29 +471,33 @@ def frame_section(gp, torch, args):
         st = gp.gp_stats(ctx, reset=True)
         return e0.elapsed_time(e1) / args.steps, st
 
-    out = {}
-    for name, variant in [("autotuned", gp.GP_AUTO), ("naive", gp.GP_NAIVE), ("hash_dynamic", gp.GP_HASH)]:
-        if name not in methods:
-            continue
-        ds = []
-        for (idx, verts, o, uni) in bufs:
-            ds.append(gp.draw_desc(idx, verts, gp.GP_SHADER_SKIN, uni, o, variant=variant,
-                                   mode=gp.GP_BATCH_DYNAMIC if variant == gp.GP_HASH else gp.GP_BATCH_STATIC))
-        frame = gp.gp_frame_create(ctx, ds)
-        ms, st = run(frame)
-        inv = st["invocations"] / max(1, st["draws"] / len(ds))
-        out[name] = {"ms_per_frame": ms, "triangles_per_s": T / (ms * 1e-3),
-                     "shading_rate": inv / sum(m.num_vertices for m in meshes)}
-        if name == "autotuned":
-            hist = {}
-            for i in range(len(ds)):
-                k = gp.gp_frame_draw_config(frame, i)
-                key = {0: "naive", 1: "warp", 2: "sort", 3: "hash", 4: "phash"}[k["variant"]]
-                key += "_dyn" if k["mode"] == 1 and k["variant"] >= 2 else ""
-                key += f"_G{k['threads_per_group']}"
-                hist[key] = hist.get(key, 0) + 1
-            out[name]["configs"] = hist
-        gp.gp_frame_destroy(frame)
+    def measure(bufs, meshes):
+        out = {}
+        for name, variant in [("autotuned", gp.GP_AUTO), ("naive", gp.GP_NAIVE), ("hash_dynamic", gp.GP_HASH)]:
+            if name not in methods:
+                continue
+            ds = []
+            for (idx, verts, o, uni) in bufs:
+                ds.append(gp.draw_desc(idx, verts, gp.GP_SHADER_SKIN, uni, o, variant=variant,
+                                       mode=gp.GP_BATCH_DYNAMIC if variant == gp.GP_HASH else gp.GP_BATCH_STATIC))
+            frame = gp.gp_frame_create(ctx, ds)
+            ms, st = run(frame)
+            inv = st["invocations"] / max(1, st["draws"] / len(ds))
+            out[name] = {"ms_per_frame": ms, "triangles_per_s": T / (ms * 1e-3),
+                         "shading_rate": inv / sum(m.num_vertices for m in meshes)}
+            if name == "autotuned":
+                hist = {}
+                for i in range(len(ds)):
+                    k = gp.gp_frame_draw_config(frame, i)
+                    key = {0: "naive", 1: "warp", 2: "sort", 3: "hash", 4: "phash"}[k["variant"]]
+                    key += "_dyn" if k["mode"] == 1 and k["variant"] >= 2 else ""
+                    key += f"_G{k['threads_per_group']}"
+                    hist[key] = hist.get(key, 0) + 1
+                out[name]["configs"] = hist
+            gp.gp_frame_destroy(frame)
+        return out
+
+    out = measure(bufs, meshes)
     # the same draws as separate submissions (no fusion), autotuned methods
     ms_sep = None
     try:
@@ -528,9 +537,20 @@ def frame_section(gp, torch, args):
             gp.gp_destroy(c)
     except Exception as e:  # reported, not fatal
         ms_sep = f"failed: {e}" if tuned else "skipped: needs the autotuned configuration"
+    # the same frame with spatially coherent bones (each vertex bound to its
+    # 4 nearest of 64 bone centres): neighbouring vertices share palette rows
+    out_nearest = None
+    if args.frame_nearest_bones:
+        del bufs, descs
+        torch.cuda.empty_cache()
+        meshes_n, bufs_n, _ = build("nearest")
+        out_nearest = measure(bufs_n, meshes_n)
+        del bufs_n
     gp.gp_destroy(ctx)
-    return {"workload": f"{len(meshes)} skinned draws, {T} triangles, one persistent launch per frame",
+    return {"workload": f"{len(meshes)} skinned draws, {T} triangles, one persistent launch per frame; bone ids "
+                        "uniform in [0, 64) ('frames') or the 4 nearest of 64 centres ('frames_nearest_bones')",
             "gen_s": gen_s, "autotune_s": tune_s, "autotune_rows": len(table), "frames": out,
+            "frames_nearest_bones": out_nearest,
             "separate_submissions_ms": ms_sep,
             "speedup_vs_separate": (ms_sep / out["autotuned"]["ms_per_frame"]) if isinstance(ms_sep, float) else None}
 

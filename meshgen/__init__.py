@@ -357,20 +357,33 @@ def mvp_uniforms(seed: int, distance: float = 3.0):
     return M.astype(np.float32), N.astype(np.float32)
 
 
-def skin_mesh(mesh: Mesh, seed: int):
+def skin_mesh(mesh: Mesh, seed: int, bones: str = "uniform"):
     """Adds bone indices/weights (64-byte layout) and a 64-bone palette.
 
-    Bones: 4 uint8 ids uniform in [0, 64); weights u_i / sum(u), u_i ~ U(0, 1].
+    Bones: 4 uint8 ids per vertex.  "uniform": each uniform in [0, 64), so
+    neighbouring vertices share no bones (the worst case for palette reads);
+    "nearest": 64 bone centres at seeded vertex positions, and each vertex
+    takes its 4 nearest centres, nearest first (neighbouring vertices share
+    bones, as in an articulated model).  Weights u_i / sum(u), u_i ~ U(0, 1].
     Palette: per bone a 3x4 row-major [R | t] with a small rotation (random
     axis, angle in [-0.2, 0.2] rad) and t in [-0.05, 0.05]^3.
     Returns (Mesh with SKIN64 vertices, palette float32 [64, 3, 4]).
     """
+    if bones not in ("uniform", "nearest"):
+        raise ValueError(f"unknown bone assignment {bones!r}")
     rng = np.random.default_rng(20_000 + seed)
     V = mesh.num_vertices
     out = np.zeros((V, 16), dtype=np.float32)
     out[:, 0:8] = mesh.vertices[:, 0:8]
-    bones = rng.integers(0, PALETTE_BONES, size=(V, 4), dtype=np.uint8)
-    out.view(np.uint8).reshape(V, 64)[:, 32:36] = bones
+    ids = rng.integers(0, PALETTE_BONES, size=(V, 4), dtype=np.uint8)
+    if bones == "nearest" and V:
+        pos = mesh.vertices[:, 0:3].astype(np.float64)
+        centres = pos[np.random.default_rng(30_000 + seed).integers(0, V, size=PALETTE_BONES)]
+        ids = np.empty((V, 4), dtype=np.uint8)
+        for a in range(0, V, 1 << 16):  # bounded memory: 65,536 vertices x 64 centres at a time
+            d = ((pos[a:a + (1 << 16), None, :] - centres[None, :, :]) ** 2).sum(axis=2)
+            ids[a:a + (1 << 16)] = np.argsort(d, axis=1, kind="stable")[:, :4]
+    out.view(np.uint8).reshape(V, 64)[:, 32:36] = ids
     u = 1.0 - rng.random(size=(V, 4))
     w = (u / u.sum(axis=1, keepdims=True)).astype(np.float32)
     out[:, 9:13] = w

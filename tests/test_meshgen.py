@@ -57,6 +57,32 @@ def test_skin_layout():
     assert np.allclose(np.einsum("bij,bkj->bik", R, R), np.eye(3), atol=1e-6)
 
 
+def test_skin_nearest_bones():
+    # "nearest": each vertex's 4 bones are the 4 closest of 64 centres placed
+    # at seeded vertex positions, nearest first; weights and palette are those
+    # of the uniform assignment
+    g = mg.geodesic_sphere(12, 3)
+    u, pal_u = mg.skin_mesh(g, 5)
+    s, pal = mg.skin_mesh(g, 5, bones="nearest")
+    assert np.array_equal(pal, pal_u)
+    assert np.array_equal(s.vertices[:, 9:13], u.vertices[:, 9:13])
+    bones, _ = mg.skin_attributes(s)
+    assert bones.max() < 64
+    assert all(len(set(b)) == 4 for b in bones.tolist())
+    pos = g.vertices[:, 0:3].astype(np.float64)
+    centres = pos[np.random.default_rng(30_000 + 5).integers(0, g.num_vertices, size=64)]
+    d = ((pos[:, None, :] - centres[None, :, :]) ** 2).sum(axis=2)
+    picked = np.take_along_axis(d, bones.astype(np.int64), axis=1)
+    assert np.all(np.diff(picked, axis=1) >= 0)  # nearest first
+    fourth = np.sort(d, axis=1)[:, 3]
+    assert np.all(picked[:, 3] <= fourth)  # no closer centre left out
+    # neighbouring vertices mostly share their nearest bone
+    a, b = g.indices.reshape(-1, 3)[:, 0], g.indices.reshape(-1, 3)[:, 1]
+    assert np.mean(bones[a, 0] == bones[b, 0]) > 0.5
+    with pytest.raises(ValueError):
+        mg.skin_mesh(g, 5, bones="random")
+
+
 def test_frame_sizes_range():
     sz = mg.frame_sizes()
     assert sz.size == 2000 and sz.min() >= 100 and sz.max() <= 50_000
