@@ -262,7 +262,9 @@ typedef struct gp_draw_desc {
   uint32_t batch_indices;     /* static S [warp 96, sort/hash/phash 255] */
   uint32_t max_unique;        /* dynamic N [256] */
   uint32_t max_tris;          /* dynamic triangle cap [floor((4N - 1) / 3)] */
-  uint32_t threads_per_group; /* sort/hash/phash: 64, 128 or 256 [256] */
+  uint32_t threads_per_group; /* sort/hash/phash: 64, 128 or 256 [256]; 256 runs the draw's batches in runs
+                                 through the two-stage pipeline of the single-draw kernel.  A batch must fit
+                                 64 KB of shared memory per block (else GP_ERR_UNSUPPORTED at frame creation) */
 } gp_draw_desc;
 
 /* The configuration a frame draw runs with (after GP_AUTO is resolved). */
