@@ -101,14 +101,17 @@ __device__ __noinline__ uint2 frame_naive(const FrameDraw& D, const Uniforms& u,
   const uint32_t ntw = min(32u, a.num_tris - tw0);
   const uint32_t t = tw0 + lane;
   if (lane < ntw) {
+    // the three corners' indices first, so their load latencies overlap
+    uint32_t id[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) id[k] = __ldg(a.idx + 3u * t + k);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      const uint32_t id = __ldg(a.idx + 3u * t + k);
       float o[K];
-      fetch_and_shade<SH>(a, u, u.palette, id, o);
+      fetch_and_shade<SH>(a, u, u.palette, id[k], o);
 #pragma unroll
       for (int c = 0; c < K; ++c) stage[lane * F + k * K + c] = o[c];
-      if (a.corner_ids != nullptr) a.corner_ids[3u * t + k] = id;
+      if (a.corner_ids != nullptr) a.corner_ids[3u * t + k] = id[k];
     }
   }
   __syncwarp();
