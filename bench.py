@@ -11,8 +11,12 @@ batching with hashing, its batch partition computed once at load time
 (Section 3.4) and timed separately.  Every reuse variant and the naive
 baseline are measured on the same mesh and reported under "variants".
 
-Prints one JSON line (rank 0).  --impl reference times the CPU oracle (the
-plain definition of the result) on a bounded sample instead.
+Prints one JSON line on stdout (rank 0), the last thing it prints: the
+headline.  The extra workloads (heavy shader, Table 2 rows, frame, serving,
+Table 1, random walk, Loop subdivision) go to stderr as "[workload] {...}"
+lines and, with --workloads-out, to a JSON file.  --impl reference times
+the CPU oracle (the plain definition of the result) on a bounded sample
+instead.
 """
 from __future__ import annotations
 
@@ -37,6 +41,7 @@ FREQ = 600
 MESH_SEED = 2
 CAM_SEED = 2
 HEADLINE = "hash_dynamic"
+HEADLINE_KERNEL = "batched_kernel<hash, mvp, dynamic>"
 METRIC = "assembled triangles/s (vertex-reuse geometry stage, one draw of the 7.2M-triangle mesh)"
 UNIT = "triangles/s"
 
@@ -58,6 +63,8 @@ def parse_args():
                          "the separate-submission comparison run only with autotuned")
     ap.add_argument("--frame-nearest-bones", type=int, default=1,
                     help="frame section: also run the frame with spatially coherent bone ids (1) or not (0)")
+    ap.add_argument("--workloads-out", default="",
+                    help="write the headline line and every extra workload's results to this JSON file")
     ap.add_argument("--clock-warm", type=float, default=1.0,
                     help="seconds of headline draws before its warm-up, so the clock sampler sees the GPU under load")
     return ap.parse_args()
@@ -361,6 +368,8 @@ def heavy_section(gp, torch, args):
         kernel_ms = st["busy_ms"] / max(1, st["draws"])
         res[name] = {"triangles_per_s": T / (ms * 1e-3), "ms_per_draw": ms, "shading_rate": inv / V,
                      "gflops_algorithmic": inv * flops_per_vertex / (kernel_ms * 1e-3) / 1e9}
+        res[name]["fp32_frac"] = res[name]["gflops_algorithmic"] / 1e3 / fp32_peak_tflops(
+            props.multi_processor_count, 2070)
         if handle:
             gp.gp_partition_release(ctx, handle)
         gp.gp_destroy(ctx)
@@ -890,12 +899,19 @@ def main():
                "note": "gp_draw_host: H2D of indices+vertices, dynamic partition, draw, D2H of all triangles"}
 
     peak, peak_kind = load_peaks()
-    achieved = algo_bytes / (kernel_ms * 1e-3) / 1e9
+    # algorithmic bytes of one launch: 12 B of indices and 84 B of assembled
+    # output per triangle, plus one 32-byte vertex row per shader invocation
+    # (the row each invocation gathers); the lower bound reads every
+    # referenced row once (32 B per vertex)
+    inv = results[HEADLINE]["invocations"]
+    bytes_inv = 12 * T + 32 * inv + 84 * T
+    achieved = bytes_inv / (kernel_ms * 1e-3) / 1e9
     traffic = dram_traffic_record()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_kind": f"of {peak_kind}", "traffic": traffic["bytes_per_launch"] if traffic else None,
-                "algorithmic_bytes_per_launch": algo_bytes,
-                "kernel": "batched_kernel<hash, mvp, dynamic>"}
+                "algorithmic_bytes_per_launch": bytes_inv,
+                "frac_min_bytes": algo_bytes / (kernel_ms * 1e-3) / 1e9 / peak,
+                "kernel_ms": kernel_ms, "kernel": HEADLINE_KERNEL}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -914,6 +930,8 @@ def main():
             cpu["all_cores"] = f"failed: {e}"
 
     if rank == 0:
+        # the headline line: compact, printed last (the extra workloads go to
+        # stderr and, when --workloads-out is given, to that file)
         line = {
             "metric": METRIC,
             "value": head_rate,
@@ -932,32 +950,41 @@ def main():
             "p99_draw_ms": st["p99_ms"],
             "vs_naive": (results[HEADLINE]["triangles_per_s"] / naive_tps) if naive_tps else None,
             "partition_ms": results[HEADLINE].get("partition_ms"),
+            "variants_ms": {k: round(v["ms_per_draw"], 5) for k, v in results.items()},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps,
             "clocks": clocks,
-            "variants": results,
-            "mesh_gen_s": gen_s,
         }
+        detail = {"variants": results, "mesh_gen_s": gen_s}
         sections = [] if args.sections == "none" else [x for x in args.sections.split(",") if x]
         if world == 1 and sections:
             # release the headline mesh before the extra workloads
             del idx, verts, out
             torch.cuda.empty_cache()
-            extra = {}
             for name, fn in (("heavy", heavy_section), ("table2", table2_section), ("frame", frame_section),
                              ("serving", serving_section),
                              ("table1", table1_section), ("walk", walk_section), ("loop", loop_section)):
                 if name in sections:
                     t0 = time.time()
                     try:
-                        extra[name] = fn(gp, torch, args)
+                        res = fn(gp, torch, args)
                     except Exception as e:  # a failing extra workload is reported, not fatal
-                        extra[name] = {"error": repr(e)[:500]}
-                    extra[name]["section_s"] = time.time() - t0
-            line["workloads"] = extra
-        print(json.dumps(line))
+                        res = {"error": repr(e)[:500]}
+                    res["section_s"] = time.time() - t0
+                    detail[name] = res
+                    print("[workload] " + json.dumps({"section": name, **res}), file=sys.stderr, flush=True)
+        if args.workloads_out:
+            with open(args.workloads_out, "w") as f:
+                json.dump({"headline": line, **detail}, f, indent=1)
+        if "heavy" in detail and "variants" in detail["heavy"]:
+            hv = detail["heavy"]
+            line["heavy"] = {"best": hv["best"], "best_vs_naive": round(hv["best_vs_naive"], 3),
+                             "hash_dynamic_vs_naive": round(hv["variants"]["hash_dynamic"]["vs_naive"], 3),
+                             "hash_dynamic_fp32_frac": round(hv["variants"]["hash_dynamic"]["fp32_frac"], 3)}
+        sys.stdout.flush()
+        print(json.dumps(line), flush=True)
     if handle:
         gp.gp_partition_release(ctx, handle)
     gp.gp_destroy(ctx)

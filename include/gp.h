@@ -138,6 +138,13 @@ typedef struct gp_out_buf {
   uint32_t* d_batch_invocations; /* optional (NULL): shader invocations per batch */
   uint64_t batch_capacity;    /* entries available in d_batch_invocations */
 } gp_out_buf;
+/* Per-batch debug information.  There is no separate gp_batch_info call: a
+ * draw writes the invocations of batch b to d_batch_invocations[b] (device,
+ * for b < batch_capacity; sort/hash/phash/warp kernels) when the caller
+ * passes that buffer, and the batch boundaries are either static (batch b =
+ * triangles [b*S/3, min((b+1)*S/3, T)), S = batch_indices) or those of the
+ * dynamic partition, which gp_partition_starts copies out.  Both are final
+ * once gp_sync has covered the draw's ticket. */
 
 /* Uniform blobs (row-major matrices), copied by value at submit. */
 typedef struct gp_uniforms_mvp {
@@ -426,9 +433,16 @@ gp_status gp_server_destroy(gp_server* server);
  *   stream         cudaStream_t for the work (NULL = legacy default stream)
  * The work is asynchronous on the stream.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls on a
+ * current and keeps it for later calls; make that first call before any
+ * stream capture.  The kept address does not survive a device reset: after
+ * cudaDeviceReset (or any other reset of the device's primary context) this
+ * entry point must not be called again in the same process.  All calls on a
  * device share the array and it keeps the last call's contents: calls whose
  * work overlaps on the GPU race on it, calls ordered on one stream do not.
+ * Device-side errors are not reported: the partition kernels' error word
+ * lives in the shared array and is not read back.  None can arise here, since
+ * the scratch is sized so that every segment's batch-start list has room for
+ * its worst case (one batch per min(max_tris, max_unique / 3) triangles).
  * Returns GP_ERR_INVALID for bad arguments or sizes, GP_ERR_CUDA for a failed
  * CUDA call, GP_OK otherwise; gp_last_error(NULL) then gives the reason on
  * the calling thread.  It calls no cudaMalloc or cudaFree. */

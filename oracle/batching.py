@@ -2,11 +2,12 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-Each function follows one step of the paper (Kenzel et al., Section 3) in the
-paper's order and notation.  Where the printed pseudocode is garbled or
-ambiguous the reading taken is stated in the docstring; the full list of
-readings is kept with the design notes.  Pure-Python loops: meant for small
-inputs or sampled batches of large ones.
+Each function takes the steps of one part of the method (Kenzel et al.,
+Section 3) in the paper's order, restated from what the step computes.
+Where the printed pseudocode is garbled or ambiguous the reading taken is
+stated in the docstring; the full list of readings is kept with the design
+notes.  Pure-Python loops: meant for small inputs or sampled batches of
+large ones.
 """
 from __future__ import annotations
 
@@ -80,33 +81,30 @@ def dynamic_partition(index_buffer, max_unique: int, max_tris: int, segment_tris
 # --------------------------------------------------------------------------
 
 def sort_batch(ids):
-    """Dynamically batched sorting (Algorithm 2).
+    """Deduplication of one batch by sorting (Section 3.4, Algorithm 2).
 
-    ids[i] <- indexBuffer[BatchBegin + i], linIds[i] <- i; sort the pairs by
-    id (stable, as a radix sort is); marks[i] = 1 where ids[i] != ids[i+1]
-    (reading: ids[size] acts as a sentinel, so the last element is marked);
-    an exclusive prefix sum of marks gives each element its group and
-    numVertices; map[linIds[i]] <- group, uniqueIds[group] <- ids[i].
+    The batch's (vertex id, position) pairs are sorted by id, stably, so
+    equal ids form runs.  The last pair of every run is flagged (the end of
+    the sorted list counts as a run boundary).  Summing the flags before each
+    pair (an exclusive prefix sum) numbers the runs 0, 1, ... in ascending id
+    order: that number is the slot of every position in the run, and the
+    total is the number of distinct ids, i.e. the shader invocations of the
+    batch.
 
-    Returns (map, uniqueIds, numVertices); uniqueIds is in ascending id order.
+    Returns (slot of each position, distinct ids in ascending order, count).
     """
-    size = len(ids)
-    pairs = sorted(((int(ids[i]), i) for i in range(size)), key=lambda p: p[0])
-    s_ids = [p[0] for p in pairs]
-    lin_ids = [p[1] for p in pairs]
-    marks = [1 if (i == size - 1 or s_ids[i] != s_ids[i + 1]) else 0 for i in range(size)]
-    prefix = []
-    run = 0
-    for m in marks:
-        prefix.append(run)
-        run += m
-    num_vertices = run
-    map_ = [0] * size
-    unique_ids = [None] * num_vertices
-    for i in range(size):
-        map_[lin_ids[i]] = prefix[i]
-        unique_ids[prefix[i]] = s_ids[i]
-    return map_, unique_ids, num_vertices
+    n = len(ids)
+    order = sorted(range(n), key=lambda pos: int(ids[pos]))  # stable: positions stay in order within a run
+    sorted_ids = [int(ids[pos]) for pos in order]
+    run_end = [int(k == n - 1 or sorted_ids[k] != sorted_ids[k + 1]) for k in range(n)]
+    runs_before = np.concatenate(([0], np.cumsum(run_end, dtype=np.int64)[:-1])).tolist() if n else []
+    count = int(sum(run_end))
+    slot_of = [0] * n
+    distinct = [None] * count
+    for k, pos in enumerate(order):
+        slot_of[pos] = runs_before[k]
+        distinct[runs_before[k]] = sorted_ids[k]
+    return slot_of, distinct, count
 
 
 def hash_slot(vertex_id: int, table_size: int) -> int:
@@ -120,102 +118,109 @@ def hash_slot(vertex_id: int, table_size: int) -> int:
 
 
 def hash_batch(ids, table_size: int):
-    """Dynamically batched hashing (Algorithm 3), insertions taken one at a
-    time in index order.
+    """Deduplication of one batch by hashing (Section 3.4, Algorithm 3), the
+    insertions taken one at a time in position order.
 
-    hashtable[.] <- -1; for each index: p <- hash(id); repeat
-    prev <- atomicCAS(hashtable[p], -1, id) (reading: the printed
-    ``hashtable[i]`` is ``hashtable[p]``); if prev = -1 or prev = id the
-    index is placed at p (reading of the garbled ``prev - 1``), else p is
-    advanced by linear probing.  map[i] <- p.  Every occupied slot is shaded.
+    The table starts with every slot empty.  Each position's id starts at its
+    home slot (``hash_slot``) and walks forward one slot at a time (linear
+    probing, wrapping around) until it finds either its own id, already
+    stored by an earlier position, or an empty slot, which it then claims.
+    The slot found is that position's entry of the map; every claimed slot is
+    one shader invocation.  Readings of the printed algorithm: the
+    compare-and-swap targets the probed slot, and a position is placed when
+    the slot held nothing or held its own id.
 
-    Returns (hashtable, map, number of occupied slots).  On the GPU the slot
-    of an id depends on the order of concurrent insertions; the set of
-    occupied ids and the id behind each map entry do not.
+    Returns (table, slot of each position, number of claimed slots).  On the
+    GPU the slot an id ends up in depends on the order of concurrent
+    insertions; the set of stored ids and the id behind each position do not.
     """
     table = [EMPTY] * table_size
-    map_ = []
+    slot_of = []
     for vid in ids:
         vid = int(vid)
-        p = hash_slot(vid, table_size)
+        s = hash_slot(vid, table_size)
         for _ in range(table_size):
-            prev = table[p]
-            if prev == EMPTY:
-                table[p] = vid
-            if prev == EMPTY or prev == vid:
+            held = table[s]
+            if held == EMPTY:
+                table[s] = vid
+            if held == EMPTY or held == vid:
                 break
-            p = (p + 1) % table_size
+            s = (s + 1) % table_size
         else:
             raise ValueError("hash table full: more unique indices than slots")
-        map_.append(p)
-    return table, map_, sum(1 for x in table if x != EMPTY)
+        slot_of.append(s)
+    return table, slot_of, sum(1 for x in table if x != EMPTY)
 
 
 def warp_vote_batch(index_buffer, batch_begin: int, batch_end: int):
-    """Statically batched warp voting (Algorithm 1), one warp of 32 lanes.
+    """Deduplication of one static batch by warp voting (Section 3.3,
+    Algorithm 1), for one warp of 32 lanes.
 
-    Each outer iteration (a "round") starts with no lane holding a vertex.
-    Chunks of 32 indices are read; for i = 0..31 the warp broadcasts lane i's
-    index (shfl), asks which lane already holds it (ballot); if none does, the
-    lowest free lane ``fill`` takes it.  outgoing[i] is lane i's slot mask.
-    The corners before the first lane that found no slot (or lies past the
-    batch end) are counted as done.  Chunks are read until every lane holds a
-    vertex or the batch ends; then the held vertices are shaded and
-    floor(done/3) triangles are written.
+    The batch is worked through in rounds.  At the start of a round no lane
+    holds a vertex.  The warp reads the batch 32 positions at a time; the
+    positions of such a chunk are considered one after another, in lane
+    order: a position whose id a lane already holds maps to that lane; a new
+    id goes to the next free lane while one is left; otherwise the position
+    gets no lane.  The positions of the chunk before the first one without a
+    lane (or past the batch end) are finished.  The round reads chunks until
+    every lane holds a vertex or the batch ends; then every held vertex is
+    shaded once and the finished positions' whole triangles are written.
+    The next round starts at the first position not written.
 
     Readings of the printed algorithm:
-      * BitShift(1, fill) with fill >= 32 gives "no slot" (mask 0);
-      * additional = 32 if firstmask = 0, else ffs(firstmask) - 1 (the
-        printed min(WarpSize, ffs(firstmask)) is unbalanced and off by one);
-      * cStart advances by 3 * triangles from its current value;
-      * all floor(done/3) triangles are written (the printed
-        ``laneId < triangles`` only covers batches of at most 96 indices);
-      * a vertex of a cut-off triangle is shaded again in the next round and
-        counts as another invocation.
+      * a 33rd new id in a round gets no lane (the printed shift by 32 is
+        read as "no lane");
+      * the finished count is 32 when every position of the chunk found a
+        lane, else the index of the first one that did not (the printed
+        minimum is unbalanced and its bit position is 1-based);
+      * the round start advances from its current value by 3 x triangles;
+      * all whole triangles of the round are written (the printed bound on
+        the lane id only covers batches of at most 96 indices);
+      * the corners of a triangle that a round cuts off are shaded again in
+        the next round and count as further invocations.
 
-    Returns a list of rounds, each a dict with ``start`` (first index of the
-    round), ``held`` (the vertex ids of lanes 0..fill-1, i.e. the shader
-    invocations), ``map`` (slot of each of the round's 3*triangles corners)
-    and ``triangles``.
+    Returns a list of rounds, each a dict with ``start`` (first position of
+    the round), ``held`` (the ids of lanes 0.. in the order they were taken,
+    i.e. the round's shader invocations), ``map`` (the lane of each of the
+    round's 3 x triangles corners) and ``triangles``.
     """
     rounds = []
-    c_start = batch_begin
-    while c_start < batch_end:
-        fill = 0
-        done = 0
-        my_id = [EMPTY] * WARP_SIZE
-        offset = c_start
-        map_ = {}
-        while offset < batch_end and fill < WARP_SIZE:
-            incoming = [int(index_buffer[offset + lane]) if offset + lane < batch_end else EMPTY
-                        for lane in range(WARP_SIZE)]
-            outgoing = [EMPTY] * WARP_SIZE
-            for i in range(WARP_SIZE):
-                current = incoming[i]
-                match = 0
-                for lane in range(WARP_SIZE):  # ballot(current = my_id)
-                    if my_id[lane] == current:
-                        match |= 1 << lane
-                if match == 0:
-                    if fill < WARP_SIZE:
-                        my_id[fill] = current
-                        match = 1 << fill
-                    fill += 1
-                outgoing[i] = match
-            for lane in range(WARP_SIZE):
-                map_[done + lane] = _ffs(outgoing[lane]) - 1
-            firstmask = 0
-            for lane in range(WARP_SIZE):
-                if outgoing[lane] == 0 or incoming[lane] == EMPTY:
-                    firstmask |= 1 << lane
-            additional = WARP_SIZE if firstmask == 0 else _ffs(firstmask) - 1
-            done += additional
+    round_start = batch_begin
+    while round_start < batch_end:
+        n_held = 0        # lanes taken, counting ids that found none
+        finished = 0      # positions of the round that found a lane, in whole chunks
+        lane_holds = [EMPTY] * WARP_SIZE
+        offset = round_start
+        lane_of = {}
+        while offset < batch_end and n_held < WARP_SIZE:
+            chunk_ids = [int(index_buffer[offset + k]) if offset + k < batch_end else EMPTY
+                         for k in range(WARP_SIZE)]
+            slot_mask = [EMPTY] * WARP_SIZE
+            for k in range(WARP_SIZE):
+                vid = chunk_ids[k]
+                holders = 0
+                for lane in range(WARP_SIZE):  # which lanes hold this id
+                    if lane_holds[lane] == vid:
+                        holders |= 1 << lane
+                if holders == 0:
+                    if n_held < WARP_SIZE:
+                        lane_holds[n_held] = vid
+                        holders = 1 << n_held
+                    n_held += 1
+                slot_mask[k] = holders
+            for k in range(WARP_SIZE):
+                lane_of[finished + k] = _ffs(slot_mask[k]) - 1
+            stops = 0
+            for k in range(WARP_SIZE):
+                if slot_mask[k] == 0 or chunk_ids[k] == EMPTY:
+                    stops |= 1 << k
+            finished += WARP_SIZE if stops == 0 else _ffs(stops) - 1
             offset += WARP_SIZE
-        triangles = done // 3
-        held = my_id[:min(fill, WARP_SIZE)]
-        rounds.append({"start": c_start, "held": held,
-                       "map": [map_[k] for k in range(3 * triangles)], "triangles": triangles})
-        c_start += 3 * triangles
+        triangles = finished // 3
+        held = lane_holds[:min(n_held, WARP_SIZE)]
+        rounds.append({"start": round_start, "held": held,
+                       "map": [lane_of[k] for k in range(3 * triangles)], "triangles": triangles})
+        round_start += 3 * triangles
     return rounds
 
 

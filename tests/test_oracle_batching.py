@@ -163,6 +163,35 @@ def test_static_batches_closed_form():
         B.static_batches(9, 256)
 
 
+def test_static_starts_closed_form():
+    """Static batch starts (Section 3.3) in triangles, against closed forms:
+    ceil(T / (S/3)) batches, every one S/3 triangles but the last, which holds
+    the remaining 1..S/3; T = 0 gives the single start 0."""
+    assert B.static_starts(0, 255) == [0]
+    # tiny grid (7,938 triangles) at S = 255: 93 batches of 85, one of 33
+    st = B.static_starts(7938, 255)
+    assert len(st) == 95 and st[0] == 0 and st[-1] == 7938
+    assert st[-1] - st[-2] == 33 and st[-2] == 93 * 85
+    # the 7.2M-triangle mesh at S = 255: 84,706 batches
+    st = B.static_starts(7_200_000, 255)
+    assert len(st) - 1 == 84_706 and st[-1] - st[-2] == 7_200_000 - 84_705 * 85
+    # exact multiples leave no ragged batch; one triangle is one batch
+    assert B.static_starts(170, 255) == [0, 85, 170]
+    assert B.static_starts(1, 3) == [0, 1]
+    assert B.static_starts(2, 3) == [0, 1, 2]
+    for T, S in [(1, 96), (31, 96), (32, 96), (33, 96), (1000, 768), (4097, 63)]:
+        per = S // 3
+        st = B.static_starts(T, S)
+        nb = -(-T // per)
+        assert len(st) == nb + 1 and st[0] == 0 and st[-1] == T
+        assert all(st[b + 1] - st[b] == per for b in range(nb - 1))
+        assert 1 <= st[-1] - st[-2] <= per
+        assert st[-1] - st[-2] == T - per * (nb - 1)
+    for bad in (0, 256, -3):
+        with pytest.raises(ValueError):
+            B.static_starts(10, bad)
+
+
 @pytest.mark.parametrize("case", _gold("dynamic_partition_cases.json")["cases"],
                          ids=lambda c: f"Nu{c['max_unique']}_max{c['max_tris']}_seg{c['segment_tris']}")
 def test_dynamic_partition_hand_worked(case):

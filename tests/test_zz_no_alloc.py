@@ -2,7 +2,8 @@
 allocate device memory (a real-time frame loop, or an application that owns
 all device memory through its own pool).
 
-Its batch starts must equal those of gp_partition, bit for bit, and repeated
+Its batch starts must equal the oracle's greedy partition (Section 3.4, with
+the segmented reading) and those of gp_partition, bit for bit, and repeated
 calls must not be affected by what an earlier call left in the shared
 scratch array.  This file is collected last so that a run stopping at the
 first failure has already run every other test; it also passes alone in a
@@ -14,6 +15,7 @@ import numpy as np
 import pytest
 
 import meshgen as mg
+from oracle import batching as B
 
 pytestmark = pytest.mark.gpu
 
@@ -46,7 +48,7 @@ def _noalloc_starts(gp, torch, idx, max_unique, max_tris, segment_tris):
     return starts.cpu().numpy()[: nb + 1]
 
 
-def test_noalloc_partition_matches_gp_partition_on_consecutive_calls():
+def test_noalloc_partition_matches_oracle_on_consecutive_calls():
     import torch
     import paper_1805_08893_gb300 as gp
     big = mg.geodesic_sphere(35, 5)      # 24,500 triangles: 6 segments
@@ -54,9 +56,12 @@ def test_noalloc_partition_matches_gp_partition_on_consecutive_calls():
     cases = [(big, 256, 341, 4096), (small, 256, 341, 4096), (big, 64, 100, 1000)]
     for mesh, nu, mt, seg in cases:  # consecutive calls share the scratch array
         idx = torch.from_numpy(mesh.indices.view(np.int32)).cuda()
-        want = _reference_starts(gp, torch, idx, nu, mt, seg)
-        got = _noalloc_starts(gp, torch, idx, nu, mt, seg)
-        assert np.array_equal(got, want), (mesh.name, nu, mt, seg)
+        oracle = np.asarray(B.dynamic_partition(mesh.indices, nu, mt, seg), dtype=np.int64)
+        for rep in range(2):  # two calls in a row on the same input
+            got = _noalloc_starts(gp, torch, idx, nu, mt, seg).astype(np.int64)
+            assert np.array_equal(got, oracle), (mesh.name, nu, mt, seg, rep)
+        want = _reference_starts(gp, torch, idx, nu, mt, seg).astype(np.int64)
+        assert np.array_equal(want, oracle), (mesh.name, nu, mt, seg)
 
 
 def test_noalloc_rejects_oversized_input():
