@@ -23,12 +23,6 @@ using namespace gp;
 
 namespace {
 thread_local std::string g_create_error;
-// Shared memory of an SM and the part the runtime reserves per block; the
-// single-draw reuse kernel sizes its output staging for at most this many
-// resident blocks (its registers allow four blocks of 256 threads).
-constexpr size_t kSmemPerSm = 228 * 1024;
-constexpr size_t kSmemReservedPerBlock = 1024;
-constexpr size_t kMaxBatchedBlocksPerSm = 4;
 // gp_draw_host: triangles per chunk (rounded to whole batches); uploads,
 // draws and read-backs of consecutive chunks overlap.  The host link bounds
 // this path; smaller chunks start the read-back earlier but add per-chunk
@@ -424,8 +418,6 @@ gp_status enqueue_draw(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* v
   // collisions, so shorter probe sequences, where the table stays small)
   a.hash_slots = cfg.hash_slots ? cfg.hash_slots : std::max(next_pow2(2 * a.ucap), std::min(next_pow2(4 * a.ucap), 1024u));
   a.hash_slots = std::max(a.hash_slots, next_pow2(threads));
-  if (dedup != DEDUP_SORT && a.max_batch_idx > 32u * threads)  // a thread numbers at most 32 positions
-    return fail(c, GP_ERR_UNSUPPORTED, "hash/phash batches may hold at most 32 x threads_per_group indices");
   if (a.hash_slots > 32768u)  // slots are stored in 15 bits
     return fail(c, GP_ERR_UNSUPPORTED, "hash_slots may be at most 32768");
   a.hash_bits = log2u(a.hash_slots);
@@ -434,33 +426,9 @@ gp_status enqueue_draw(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* v
     const uint32_t pb = std::max(1u, log2u(a.sort_n));
     a.sort_pos_bits = (pb < 32 && (uint64_t)a.num_verts + 1 < (1ull << (32 - pb))) ? pb : 0u;
   }
-  // staging for the output: the largest chunk (the whole batch, or a half,
-  // quarter, ... of it) that keeps the most blocks resident on an SM, up to
-  // four (beyond that the registers limit them)
-  {
-    auto resident = [&](uint32_t chunk) {
-      a.out_chunk = chunk;
-      const size_t need = batched_smem_bytes(dedup, (int)shader, a, (int)threads) + kSmemReservedPerBlock;
-      return std::min<size_t>(kMaxBatchedBlocksPerSm, kSmemPerSm / need);
-    };
-    const uint32_t whole = (a.max_batch_idx + 2) / 3;
-    uint32_t best = whole;
-    size_t best_blocks = resident(whole);
-    for (uint32_t chunk = whole; chunk > 32;) {
-      chunk = (chunk + 1) / 2;
-      const size_t blocks = resident(chunk);
-      if (blocks > best_blocks) {
-        best = chunk;
-        best_blocks = blocks;
-      }
-    }
-    a.out_chunk = best;
-  }
-  if (const char* oc = std::getenv("GP_OUT_CHUNK")) {  // tuning override
-    const long v = std::strtol(oc, nullptr, 10);
-    if (v > 0) a.out_chunk = std::min<uint32_t>((uint32_t)v, (a.max_batch_idx + 2) / 3);
-  }
-  const size_t smem = batched_smem_bytes(dedup, (int)shader, a, (int)threads);
+  // the kernel splits its block into producer and consumer warps: at least two warps
+  const uint32_t block = std::max(64u, threads);
+  const size_t smem = reuse_smem_bytes(dedup, (int)shader, a, (int)block);
   if (smem > 227 * 1024)
     return fail(c, GP_ERR_UNSUPPORTED, "batch configuration needs more than 227 KB of shared memory");
   const uint64_t key = (2ull << 56) | ((uint64_t)dedup << 48) | ((uint64_t)dyn << 47) | ((uint64_t)shader << 40) |
@@ -470,20 +438,18 @@ gp_status enqueue_draw(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* v
   if (it != c->occ.end()) {
     bpsm = it->second;
   } else {
-    bpsm = batched_blocks_per_sm(dedup, dyn, (int)shader, (int)threads, smem);
+    bpsm = reuse_blocks_per_sm(dedup, dyn, (int)shader, (int)block, smem);
     c->occ[key] = bpsm;
   }
   if (bpsm <= 0) return fail(c, GP_ERR_UNSUPPORTED, "draw kernel cannot be resident with this configuration");
   uint64_t grid = (uint64_t)c->sms * bpsm;
   if (!dyn) grid = std::min<uint64_t>(grid, a.num_batches);
   if (std::getenv("GP_VERBOSE") && c->logged.insert(key).second)
-    std::fprintf(stderr,
-                 "[gp] batched dedup=%d dyn=%d shader=%u threads=%u smem=%zu blocks/SM=%d grid=%llu slots=%u "
-                 "chunk=%u\n",
-                 dedup, (int)dyn, shader, threads, smem, bpsm, (unsigned long long)grid, a.hash_slots, a.out_chunk);
+    std::fprintf(stderr, "[gp] reuse dedup=%d dyn=%d shader=%u threads=%u smem=%zu blocks/SM=%d grid=%llu slots=%u\n",
+                 dedup, (int)dyn, shader, block, smem, bpsm, (unsigned long long)grid, a.hash_slots);
   t.device_counts = true;
-  GP_CUDA(c, launch_batched(dedup, dyn, a, u, (int)shader, (int)threads, (int)std::max<uint64_t>(grid, 1), smem,
-                            c->stream));
+  GP_CUDA(c, launch_reuse(dedup, dyn, a, u, (int)shader, (int)block, (int)std::max<uint64_t>(grid, 1), smem,
+                          c->stream));
   return GP_OK;
 }
 

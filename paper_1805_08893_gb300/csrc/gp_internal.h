@@ -101,10 +101,11 @@ cudaError_t launch_warp(const DrawArgs& a, const Uniforms& u, int shader, int wa
 int warp_kernel_blocks_per_sm(int shader, int warps_per_block);
 size_t warp_kernel_smem(int shader, int warps_per_block, uint32_t batch_idx);
 
-size_t batched_smem_bytes(int dedup, int shader, const DrawArgs& a, int threads);
-cudaError_t launch_batched(int dedup, bool dynamic, const DrawArgs& a, const Uniforms& u, int shader,
-                           int threads, int grid, size_t smem, cudaStream_t s);
-int batched_blocks_per_sm(int dedup, bool dynamic, int shader, int threads, size_t smem);
+// Single-draw sort/hash/phash kernel (gp_reuse.cu).
+size_t reuse_smem_bytes(int dedup, int shader, const DrawArgs& a, int threads);
+cudaError_t launch_reuse(int dedup, bool dynamic, const DrawArgs& a, const Uniforms& u, int shader,
+                         int threads, int grid, size_t smem, cudaStream_t s);
+int reuse_blocks_per_sm(int dedup, bool dynamic, int shader, int threads, size_t smem);
 
 size_t partition_smem_bytes(const PartitionArgs& p, int warps);
 cudaError_t launch_partition(const PartitionArgs& p, int warps_per_block, cudaStream_t s);
