@@ -26,9 +26,11 @@
 //   consumer warps (the second half) take batch j from its slot: each unique
 //     vertex is shaded once, in place in its row; then every warp assembles
 //     its groups (4 corners' shaded rows per lane) through a per-warp staging
-//     area (a transpose) into coalesced 16-byte streaming stores -- only the
-//     float4 at the batch's two ends that the neighbouring batch shares are
-//     written float by float -- and arrives on the slot's "empty" mbarrier.
+//     area (a transpose): with 7 floats per corner a span that lies inside
+//     the batch leaves in one bulk (TMA) store per warp, otherwise through
+//     coalesced 16-byte streaming stores -- only the float4 at the batch's
+//     two ends that the neighbouring batch shares are written float by
+//     float -- and arrives on the slot's "empty" mbarrier.
 //
 // Deduplication (shared-memory atomics) and shading/assembly (shared-memory
 // reads, FP32, stores) thus overlap across warps instead of alternating
@@ -126,13 +128,15 @@ __device__ __forceinline__ void named_sync(uint32_t id, uint32_t nthreads) {
 }
 
 // Bounded wait on an mbarrier phase that also gives up once another thread
-// has stopped the block (*abort != 0).  Sets EBIT_TIMEOUT and *abort when
-// the limit runs out.
+// has stopped the block (*abort != 0).  The waiting thread sleeps in steps
+// of at most 50 us (waking as soon as the phase completes), so a waiting
+// warp takes no issue slots from the other role; after 2^14 steps (at most
+// ~0.8 s) it sets EBIT_TIMEOUT and *abort and gives up.
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, volatile uint32_t* abort,
                                               uint32_t* err) {
-  for (uint32_t it = 0; it < (1u << 22); ++it) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if ((it & 31u) == 31u && *abort) return false;
+  for (uint32_t it = 0; it < (1u << 14); ++it) {
+    if (mbar_try_wait_sleep(bar, parity, 50000u)) return true;
+    if (*abort) return false;
   }
   atomicOr(err, EBIT_TIMEOUT);
   *abort = 1u;
@@ -455,6 +459,7 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
     const uint32_t ctid = tid - NP, cw = warp - NPW;
     float4* stage = reinterpret_cast<float4*>(smem + L.off_stage) + cw * 32u * K;
     unsigned long long inv_total = 0, nbatches = 0;
+    bool bulk_pending = false;  // a bulk store of this warp may still read its staging area
     uint32_t fph = 0u;  // bit s: parity of full[s]
     uint32_t j = 0;
     for (uint32_t b = blockIdx.x; b < nb; b += stride, ++j) {
@@ -524,13 +529,29 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
               if (g < ngroups && p >= pad && p < pad + n) a.corner_ids[base + p] = uniq[r];
             }
           }
-          if (K == 7)
+          const size_t F0 = (size_t)K * (base + 4 * gw);  // first float of the warp's span (16-byte aligned)
+          const bool interior = F0 >= f_lo && F0 + 128 * K <= f_hi;  // the whole span lies in the batch
+          if (K == 7) {
+            if (bulk_pending) {  // the last bulk store must have read the staging area
+              if (lane == 0) bulk_wait_read<0>();
+              __syncwarp();
+              bulk_pending = false;
+            }
 #pragma unroll
             for (int jj = 0; jj < 7; ++jj)
               stage[stage_put<K>(lane, jj)] = make_float4(f[4 * jj], f[4 * jj + 1], f[4 * jj + 2], f[4 * jj + 3]);
+            if (interior) {  // the span in one bulk (TMA) store, in output order in the staging area
+              fence_proxy_async_smem();
+              __syncwarp();
+              if (lane == 0) {
+                bulk_store(a.out + F0, stage, 128 * K * 4);
+                bulk_commit();
+              }
+              bulk_pending = true;
+              continue;
+            }
+          }
           __syncwarp();
-          const size_t F0 = (size_t)K * (base + 4 * gw);  // first float of the warp's span (16-byte aligned)
-          const bool interior = F0 >= f_lo && F0 + 128 * K <= f_hi;  // the whole span lies in the batch
 #pragma unroll
           for (int jj = 0; jj < K; ++jj) {
             const float4 v = stage[stage_get<K>(32 * jj + lane)];
@@ -549,6 +570,7 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
       }
       mbar_arrive(&bars[4 + s]);  // this thread is done with the slot
     }
+    if (lane == 0) bulk_wait_all<0>();  // this warp's bulk stores are complete
     if (ctid == 0 && nbatches) {
       atomicAdd(a.counters + CNT_INVOCATIONS, inv_total);
       atomicAdd(a.counters + CNT_BATCHES, nbatches);
