@@ -159,57 +159,72 @@ __device__ __forceinline__ T bitonic_keep(T x, T y, uint32_t i, uint32_t j, uint
   return take_min ? mn : mx;
 }
 
-// Bitonic sort of keys[0..N), N a power of two.  With N = 4 * NT every
-// thread keeps 4 consecutive keys in registers: stages with j <= 2 stay in
-// the thread, 4 <= j <= 64 exchange within the warp by shuffles (partner lane
-// = lane ^ j/4), and only j >= 128 goes through shared memory.  Otherwise the
-// network runs in shared memory; for j <= 32 the pairs touched by one warp
-// stay inside that warp's 64-key blocks (i = 2t - (t mod j), t = 32q + r), so
-// those stages need only a warp barrier.  Leaves the sorted keys in keys[].
+// Bitonic network over N = E * NT keys with E consecutive keys per thread
+// in registers: stages with j < E stay in the thread, E <= j < 32 E exchange
+// within the warp by shuffles (partner lane = lane ^ j/E), and only
+// j >= 32 E goes through shared memory.
+template <int E, class T, class Sync>
+__device__ __forceinline__ void bitonic_sort_regs(T* keys, uint32_t N, uint32_t tid, Sync sync) {
+  T r[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) r[e] = keys[E * tid + e];
+  for (uint32_t k = 2; k <= N; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      if (j >= 32u * E) {
+        sync();  // every thread has read the previous contents
+#pragma unroll
+        for (int e = 0; e < E; ++e) keys[E * tid + e] = r[e];
+        sync();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const uint32_t i = E * tid + e;
+          r[e] = bitonic_keep(r[e], keys[i ^ j], i, j, k);
+        }
+      } else if (j >= (uint32_t)E) {
+        const uint32_t lm = j / E;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const T y = __shfl_xor_sync(kFull, r[e], lm);
+          r[e] = bitonic_keep(r[e], y, E * tid + e, j, k);
+        }
+      } else {
+        // j < E: the partner is in this thread (j is 1, 2 or 4, each with
+        // compile-time register indices)
+        T q[E];
+        if (j == 1) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) q[e] = bitonic_keep(r[e], r[e ^ 1], E * tid + e, 1u, k);
+        } else if (j == 2) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) q[e] = bitonic_keep(r[e], r[e ^ 2], E * tid + e, 2u, k);
+        } else {
+#pragma unroll
+          for (int e = 0; e < E; ++e) q[e] = bitonic_keep(r[e], r[(e ^ 4) & (E - 1)], E * tid + e, 4u, k);
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) r[e] = q[e];
+      }
+    }
+  }
+  sync();
+#pragma unroll
+  for (int e = 0; e < E; ++e) keys[E * tid + e] = r[e];
+  sync();
+}
+
+// Bitonic sort of keys[0..N), N a power of two.  With N = 4 NT or 8 NT the
+// keys stay in registers (bitonic_sort_regs).  Otherwise the network runs
+// in shared memory; for j <= 32 the pairs touched by one warp stay inside
+// that warp's 64-key blocks (i = 2t - (t mod j), t = 32q + r), so those
+// stages need only a warp barrier.  Leaves the sorted keys in keys[].
 template <class T, class Sync>
 __device__ __forceinline__ void bitonic_sort(T* keys, uint32_t N, uint32_t tid, uint32_t NT, Sync sync) {
   if (N == 4 * NT) {
-    T r[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e) r[e] = keys[4 * tid + e];
-    for (uint32_t k = 2; k <= N; k <<= 1) {
-      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-        if (j >= 128) {
-          sync();  // every thread has read the previous contents
-#pragma unroll
-          for (int e = 0; e < 4; ++e) keys[4 * tid + e] = r[e];
-          sync();
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const uint32_t i = 4 * tid + e;
-            r[e] = bitonic_keep(r[e], keys[i ^ j], i, j, k);
-          }
-        } else if (j >= 4) {
-          const uint32_t lm = j >> 2;
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const T y = __shfl_xor_sync(kFull, r[e], lm);
-            r[e] = bitonic_keep(r[e], y, 4 * tid + e, j, k);
-          }
-        } else if (j == 2) {
-          T s[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) s[e] = bitonic_keep(r[e], r[e ^ 2], 4 * tid + e, 2, k);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) r[e] = s[e];
-        } else {
-          T s[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) s[e] = bitonic_keep(r[e], r[e ^ 1], 4 * tid + e, 1, k);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) r[e] = s[e];
-        }
-      }
-    }
-    sync();
-#pragma unroll
-    for (int e = 0; e < 4; ++e) keys[4 * tid + e] = r[e];
-    sync();
+    bitonic_sort_regs<4>(keys, N, tid, sync);
+    return;
+  }
+  if (N == 8 * NT) {
+    bitonic_sort_regs<8>(keys, N, tid, sync);
     return;
   }
   for (uint32_t k = 2; k <= N; k <<= 1) {

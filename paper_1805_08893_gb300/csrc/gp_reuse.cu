@@ -51,12 +51,13 @@ struct ReuseLayout {
 
 __host__ __device__ inline uint32_t reuse_align16(uint32_t x) { return (x + 15u) & ~15u; }
 
-// Producer warps of a block of NT threads (at least 64): five eighths,
-// rounded down (5 of 8 warps); the rest are consumers.  Deduplication is
-// the longer chain of dependent shared-memory round trips, so it gets more
-// warps.
-__host__ __device__ inline uint32_t reuse_producer_warps(uint32_t NT) {
-  const uint32_t w = NT / 32, p = (5 * w) / 8;
+// Producer warps of a block of NT threads (at least 64): hash/phash five
+// eighths, rounded down (5 of 8 warps) -- deduplication is the longer chain
+// of dependent shared-memory round trips; sort half (4 of 8), so that a
+// 1024-key network keeps 8 keys per producer thread in registers.  The rest
+// are consumers.
+__host__ __device__ inline uint32_t reuse_producer_warps(uint32_t NT, int dedup) {
+  const uint32_t w = NT / 32, p = dedup == DEDUP_SORT ? w / 2 : (5 * w) / 8;
   return p < 1 ? 1 : (p >= w ? w - 1 : p);
 }
 // Groups (4 positions) a producer thread inserts per pass, all CAS in flight.
@@ -65,7 +66,7 @@ constexpr int kGroupsPerPass = 2;
 // Shared-memory layout for NT threads.  K: floats per output corner.
 __host__ __device__ inline ReuseLayout reuse_layout(int dedup, int shader, const DrawArgs& a, uint32_t NT) {
   const uint32_t K = shader == 2 ? 8u : 7u;
-  const uint32_t consumer_warps = NT / 32 - reuse_producer_warps(NT);
+  const uint32_t consumer_warps = NT / 32 - reuse_producer_warps(NT, dedup);
   ReuseLayout L;
   uint32_t o = 0;
   L.off_bar = o; o += 64;       // window[2], full[2], empty[2]
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
   constexpr uint32_t RB = ShaderTraits<SH>::kSkin ? 64u : 32u;
   extern __shared__ __align__(128) unsigned char smem[];
   const uint32_t tid = threadIdx.x, NT = blockDim.x, lane = tid & 31u, warp = tid >> 5;
-  const uint32_t NPW = reuse_producer_warps(NT), NP = 32 * NPW, NC = NT - NP;
+  const uint32_t NPW = reuse_producer_warps(NT, DEDUP), NP = 32 * NPW, NC = NT - NP;
   const ReuseLayout L = reuse_layout(DEDUP, SH, a, NT);
   const uint32_t nb = DYN ? *a.num_batches_dev : a.num_batches;
   if (blockIdx.x >= nb) return;
