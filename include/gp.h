@@ -416,6 +416,25 @@ gp_status gp_server_stats(gp_server* server, gp_serve_stats* out, int reset);
 /* Waits for all requests, stops the thread and frees device memory. */
 gp_status gp_server_destroy(gp_server* server);
 
+/* Failure injection, for testing the error paths without a GPU fault.
+ * The paper has no counterpart.  what:
+ *   GP_TEST_FAIL_ALLOC    the context's next `count` device allocations
+ *                         (partition buffers, host-draw staging, the
+ *                         multi-kernel comparator's rows) report an
+ *                         exhausted device without allocating; the call that
+ *                         needed them returns GP_ERR_OOM and the context
+ *                         stays usable;
+ *   GP_TEST_STALL_WINDOW  the next `count` sort/hash/phash draws announce
+ *                         each block's first index window on its mbarrier
+ *                         but never copy it, so the kernel's bounded wait
+ *                         runs out (about a second) and the block stops;
+ *                         gp_sync reports GP_ERR_TIMEOUT for the draw and
+ *                         later draws run normally.
+ * count = 0 clears the injection.  GP_ERR_INVALID for an unknown kind or a
+ * NULL context. */
+enum { GP_TEST_FAIL_ALLOC = 1, GP_TEST_STALL_WINDOW = 2 };
+gp_status gp_test_inject(gp_ctx* ctx, uint32_t what, uint32_t count);
+
 /* Dynamic partition without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that must not allocate
  * device memory -- a real-time frame loop, where cudaMalloc can synchronise

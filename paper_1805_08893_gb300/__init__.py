@@ -22,7 +22,7 @@ __all__ = [
     "gp_last_error", "gp_status_string", "gp_partition_noalloc", "gp_frame_create", "gp_frame_submit",
     "gp_frame_set_uniforms", "gp_frame_draw_config", "gp_frame_destroy", "gp_autotune", "gp_autotune_table",
     "gp_autotune_set_table", "draw_desc", "gp_server_create", "gp_server_add_mesh", "gp_server_submit",
-    "gp_server_replay", "gp_server_wait", "gp_server_latency", "gp_server_stats", "gp_server_destroy", "uniforms_mvp", "uniforms_skin", "uniforms_envelope", "uniforms_load",
+    "gp_server_replay", "gp_server_wait", "gp_server_latency", "gp_server_stats", "gp_server_destroy", "uniforms_mvp", "uniforms_skin", "uniforms_envelope", "uniforms_load", "gp_test_inject",
     "Context", "lib", "library_path",
 ]
 
@@ -34,6 +34,7 @@ GP_BATCH_STATIC, GP_BATCH_DYNAMIC = 0, 1
 GP_SHADER_MVP, GP_SHADER_SKIN, GP_SHADER_ENVELOPE, GP_SHADER_LOAD = range(4)
 GP_VFMT_PNU32, GP_VFMT_SKIN64 = 0, 1
 GP_SEGMENT_NONE = 0xFFFFFFFF
+GP_TEST_FAIL_ALLOC, GP_TEST_STALL_WINDOW = 1, 2
 
 VARIANTS = {"naive": GP_NAIVE, "warp": GP_WARP, "sort": GP_SORT, "hash": GP_HASH, "phash": GP_PHASH,
             "multi": GP_MULTI}
@@ -174,6 +175,7 @@ def _load():
         "gp_last_error": ([P], ctypes.c_char_p),
         "gp_status_string": ([I], ctypes.c_char_p),
         "gp_partition_noalloc": ([P, U64, U32, U32, U32, P, U64, P, P], I),
+        "gp_test_inject": ([P, U32, U32], I),
         "gp_frame_create": ([P, ctypes.POINTER(gp_draw_desc), U32, ctypes.POINTER(P)], I),
         "gp_frame_submit": ([P, ctypes.POINTER(U64)], I),
         "gp_frame_set_uniforms": ([P, U32, P, U32], I),
@@ -332,6 +334,12 @@ def gp_draw_host(ctx, indices, vertices, shader_id, uniforms, out, fmt=None):
                          ctypes.cast(ctypes.byref(uniforms), ctypes.c_void_p), ctypes.sizeof(uniforms),
                          addr(out), nbytes(out))
     _check(s, ctx)
+
+
+def gp_test_inject(ctx, what, count=1):
+    """gp_test_inject: failure injection for tests (GP_TEST_FAIL_ALLOC,
+    GP_TEST_STALL_WINDOW)."""
+    _check(lib.gp_test_inject(ctx, what, count), ctx)
 
 
 def gp_partition_noalloc(indices, max_unique, max_tris, segment_tris, starts, num_batches, stream=None):

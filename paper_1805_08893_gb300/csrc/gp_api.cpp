@@ -77,6 +77,17 @@ gp_status fail(gp_ctx* c, gp_status s, const std::string& msg) {
   return s;
 }
 
+// Device allocation on behalf of a context; reports an exhausted device
+// without allocating while failure injection asks for it (gp_test_inject).
+cudaError_t ctx_malloc(gp_ctx* c, void** p, size_t bytes) {
+  if (c && c->test_fail_allocs) {
+    --c->test_fail_allocs;
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
+}
+
 gp_status cuda_fail(gp_ctx* c, cudaError_t e, const char* what) {
   return fail(c, e == cudaErrorMemoryAllocation ? GP_ERR_OOM : GP_ERR_CUDA,
               std::string(what) + ": " + cudaGetErrorString(e));
@@ -287,9 +298,9 @@ gp_status size_partition(gp_ctx* c, Partition& p, uint64_t num_idx, bool reuse_a
     p.d_starts = nullptr;
     p.d_seg = nullptr;
     void* ptr = nullptr;
-    GP_CUDA(c, cudaMalloc(&ptr, need_starts + 16));
+    GP_CUDA(c, ctx_malloc(c, &ptr, need_starts + 16));
     p.d_starts = static_cast<uint32_t*>(ptr);
-    GP_CUDA(c, cudaMalloc(&ptr, need_seg + 16));
+    GP_CUDA(c, ctx_malloc(c, &ptr, need_seg + 16));
     p.d_seg = static_cast<uint32_t*>(ptr);
     p.max_batches = (uint32_t)max_b;
   }
@@ -353,7 +364,7 @@ gp_status enqueue_draw(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* v
       if (c->d_shaded) cudaFree(c->d_shaded);
       c->d_shaded = nullptr;
       c->shaded_cap = 0;
-      cudaError_t e = cudaMalloc(&c->d_shaded, V * 2 * sizeof(float4));
+      cudaError_t e = ctx_malloc(c, reinterpret_cast<void**>(&c->d_shaded), V * 2 * sizeof(float4));
       if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc (shaded vertex rows)");
       c->shaded_cap = V;
     }
@@ -447,6 +458,10 @@ gp_status enqueue_draw(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* v
   if (std::getenv("GP_VERBOSE") && c->logged.insert(key).second)
     std::fprintf(stderr, "[gp] reuse dedup=%d dyn=%d shader=%u threads=%u smem=%zu blocks/SM=%d grid=%llu slots=%u\n",
                  dedup, (int)dyn, shader, block, smem, bpsm, (unsigned long long)grid, a.hash_slots);
+  if (c->test_stall_draws) {  // failure injection: this draw's bounded window wait runs out
+    --c->test_stall_draws;
+    a.test_stall = 1;
+  }
   t.device_counts = true;
   GP_CUDA(c, launch_reuse(dedup, dyn, a, u, (int)shader, (int)block, (int)std::max<uint64_t>(grid, 1), smem,
                           c->stream));
@@ -526,7 +541,7 @@ gp_status ensure_buf(gp_ctx* c, void** p, size_t* cap, size_t need) {
   if (*p) cudaFree(*p);
   *p = nullptr;
   *cap = 0;
-  GP_CUDA(c, cudaMalloc(p, std::max<size_t>(need, 256)));
+  GP_CUDA(c, ctx_malloc(c, p, std::max<size_t>(need, 256)));
   *cap = std::max<size_t>(need, 256);
   return GP_OK;
 }
@@ -715,6 +730,16 @@ gp_status gp_sync(gp_ctx* c, uint64_t ticket, uint32_t timeout_ms) {
   std::lock_guard<std::mutex> lk(c->mu);
   cudaSetDevice(c->device);
   return sync_locked(c, ticket, timeout_ms);
+}
+
+gp_status gp_test_inject(gp_ctx* c, uint32_t what, uint32_t count) {
+  if (!c) return fail(nullptr, GP_ERR_INVALID, "gp_test_inject: ctx is NULL");
+  std::lock_guard<std::mutex> lk(c->mu);
+  switch (what) {
+    case GP_TEST_FAIL_ALLOC: c->test_fail_allocs = count; return GP_OK;
+    case GP_TEST_STALL_WINDOW: c->test_stall_draws = count; return GP_OK;
+    default: return fail(c, GP_ERR_INVALID, "gp_test_inject: unknown failure kind");
+  }
 }
 
 gp_status gp_stats(gp_ctx* c, gp_stats_t* out, int reset) {

@@ -91,6 +91,10 @@ struct gp_ctx {
   // errors
   gp_status last_status = GP_OK;
   std::string last_error;
+  // failure injection (gp_test_inject): allocations to fail, draws whose
+  // kernel is to stall on its first index window
+  uint32_t test_fail_allocs = 0;
+  uint32_t test_stall_draws = 0;
   // host-draw staging
   void* h_idx = nullptr;
   size_t h_idx_cap = 0;

@@ -69,6 +69,7 @@ struct DrawArgs {
   // bookkeeping
   unsigned long long* counters;  // CNT_* slots
   uint32_t* err;                 // error word
+  uint32_t test_stall;           // 1: failure injection, the first index window is never copied
 };
 
 struct PartitionArgs {

@@ -226,7 +226,10 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
     mbar_arrive_expect_tx(&bars[buf], bytes);
     if (bytes) bulk_load(winbuf + buf * L.win_words, a.idx + base, bytes, &bars[buf]);
   };
-  if (tid == 0) issue_window(blockIdx.x, 0);
+  if (tid == 0) {
+    if (a.test_stall) mbar_arrive_expect_tx(&bars[0], 16);  // failure injection: bytes that never come
+    else issue_window(blockIdx.x, 0);
+  }
   __syncthreads();
   const uint32_t stride = gridDim.x;
 
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
     // ======================= producers =======================
     const uint32_t pw = warp;
     uint32_t wph = 0u, eph = 0u;  // bit s: parity of window[s] / empty[s]
-    bool window_pending = false;  // thread 0: a window copy may be in flight into pending_buf
+    bool window_pending = tid == 0;  // thread 0: a window copy may be in flight into pending_buf
     uint32_t pending_buf = 0;
     uint32_t j = 0;
     for (uint32_t b = blockIdx.x; b < nb; b += stride, ++j) {
@@ -453,8 +456,9 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
     }
     // never leave a copy in flight into this block's shared memory
     cp_async_wait<0>();
-    if (tid == 0 && window_pending && *abort_flag)
-      mbar_wait_bounded(&bars[pending_buf], (wph >> pending_buf) & 1u, a.err);
+    if (tid == 0 && window_pending && *abort_flag)  // sleeps in steps, at most ~0.8 s
+      for (uint32_t it = 0; it < (1u << 14); ++it)
+        if (mbar_try_wait_sleep(&bars[pending_buf], (wph >> pending_buf) & 1u, 50000u)) break;
   } else {
     // ======================= consumers =======================
     const uint32_t ctid = tid - NP, cw = warp - NPW;

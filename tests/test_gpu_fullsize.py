@@ -50,3 +50,46 @@ def test_full_size_baselines(big, variant):
     assert r.stats["invocations"] == (3 * mesh.num_tris if variant == "naive" else mesh.num_vertices)
     tris = np.sort(np.random.default_rng(6).choice(mesh.num_tris, size=20000, replace=False))
     assert_attrs_close(r.out[tris], S.draw(mesh, S.SHADER_MVP, uni_o, tris=tris), S.SHADER_MVP, mesh)
+
+
+# ---------------------------------------------------------------------------
+# the heavy-shader workload at its bench size: the envelope shader on the
+# 2M-triangle geodesic sphere (f = 316), as bench.py's heavy section draws it
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def heavy():
+    mesh = mg.geodesic_sphere(316, 4)
+    starts = B.dynamic_partition(mesh.indices, 256, 341, 4096)
+    return mesh, starts
+
+
+@pytest.mark.parametrize("variant", ["hash", "phash", "sort"])
+def test_envelope_bench_size_dynamic(heavy, variant):
+    mesh, starts = heavy
+    uni, uni_o = uniforms_for(mesh, S.SHADER_ENVELOPE)
+    r = draw_gpu(mesh, variant, S.SHADER_ENVELOPE, "dynamic", uni, threads_per_group=256)
+    assert r.status == 0
+    assert r.starts.tolist() == starts
+    assert np.array_equal(r.ids, mesh.indices)
+    # sort/hash/phash shade each batch's distinct ids once: the plain definition
+    want = B.unique_per_batch(mesh.indices, starts)
+    assert np.array_equal(r.inv, want)
+    assert r.stats["invocations"] == int(want.sum())
+    tris = np.sort(np.random.default_rng(7).choice(mesh.num_tris, size=20000, replace=False))
+    assert_attrs_close(r.out[tris], S.draw(mesh, S.SHADER_ENVELOPE, uni_o, tris=tris), S.SHADER_ENVELOPE, mesh)
+
+
+@pytest.mark.parametrize("variant", ["naive", "multi", "warp"])
+def test_envelope_bench_size_baselines(heavy, variant):
+    mesh, _ = heavy
+    uni, uni_o = uniforms_for(mesh, S.SHADER_ENVELOPE)
+    r = draw_gpu(mesh, variant, S.SHADER_ENVELOPE, "static", uni)
+    assert r.status == 0
+    assert np.array_equal(r.ids, mesh.indices)
+    if variant == "naive":
+        assert r.stats["invocations"] == 3 * mesh.num_tris
+    elif variant == "multi":
+        assert r.stats["invocations"] == mesh.num_vertices
+    tris = np.sort(np.random.default_rng(8).choice(mesh.num_tris, size=20000, replace=False))
+    assert_attrs_close(r.out[tris], S.draw(mesh, S.SHADER_ENVELOPE, uni_o, tris=tris), S.SHADER_ENVELOPE, mesh)
