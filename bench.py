@@ -41,7 +41,7 @@ FREQ = 600
 MESH_SEED = 2
 CAM_SEED = 2
 HEADLINE = "hash_dynamic"
-HEADLINE_KERNEL = "batched_kernel<hash, mvp, dynamic>"
+HEADLINE_KERNEL = "reuse_kernel<hash, mvp, dynamic>"
 METRIC = "assembled triangles/s (vertex-reuse geometry stage, one draw of the 7.2M-triangle mesh)"
 UNIT = "triangles/s"
 
