@@ -19,6 +19,7 @@ enum : int {
   CNT_INVOCATIONS = 0,
   CNT_BATCHES = 1,
   CNT_UNIQUE = 2,
+  CNT_WORK = 3,  // batches claimed beyond the first wave (single-draw reuse kernel)
   CNT_SLOTS = 8,
 };
 

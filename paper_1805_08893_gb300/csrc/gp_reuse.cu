@@ -2,8 +2,10 @@
 // parallel hashing (Section 3.4), over static batches (Section 3.3) or the
 // dynamic batches of the partition (Section 3.4).
 //
-// Each block is persistent (grid = SMs x resident blocks) and takes the
-// batches blockIdx.x, blockIdx.x + gridDim.x, ...  Its warps have two roles
+// Each block is persistent (grid = SMs x resident blocks): it starts with
+// batch blockIdx.x and then claims batches gridDim.x, gridDim.x + 1, ...
+// from a per-draw counter, one at a time, so blocks that run faster take
+// more batches and all finish together.  Its warps have two roles
 // that run side by side, handing batches over through a two-deep ring of
 // shared-memory slots guarded by mbarriers ("full": deduplicated, rows
 // landed; "empty": assembled, slot free):
@@ -41,6 +43,7 @@
 
 namespace gp {
 
+constexpr uint32_t kNoBatch = 0xFFFFFFFFu;  // a ring slot that ends the block's work
 constexpr uint32_t kBarProducers = 1;  // named barrier of the producer warps
 constexpr uint32_t kBarConsumers = 2;  // named barrier of the consumer warps
 
@@ -70,7 +73,8 @@ __host__ __device__ inline ReuseLayout reuse_layout(int dedup, int shader, const
   ReuseLayout L;
   uint32_t o = 0;
   L.off_bar = o; o += 64;       // window[2], full[2], empty[2]
-  L.off_misc = o; o += 64 * 4;  // [0], [1]: unique counters of the two slots; [2]: abort; [8..]: sort scan
+  L.off_misc = o; o += 64 * 4;  // [0], [1]: unique counters of the two slots; [2]: abort; [4], [5]: each slot's
+                                // batch; [6], [7]: the producers' next batch; [8..]: sort scan
   L.groups = (a.max_batch_idx + 6) / 4;  // pad (<= 3) + indices, in 4-word groups
   L.win_words = 4 * L.groups;
   L.off_win = o; o += 2 * L.win_words * 4;
@@ -239,10 +243,16 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
     uint32_t wph = 0u, eph = 0u;  // bit s: parity of window[s] / empty[s]
     bool window_pending = tid == 0;  // thread 0: a window copy may be in flight into pending_buf
     uint32_t pending_buf = 0;
-    uint32_t j = 0;
-    for (uint32_t b = blockIdx.x; b < nb; b += stride, ++j) {
+    uint32_t b = blockIdx.x;  // the batch this iteration deduplicates
+    for (uint32_t j = 0;; ++j) {
       const uint32_t s = j & 1u;
       if (*abort_flag) break;
+      if (b >= nb) {  // no batch left: hand the consumers a slot that says so
+        if (j >= 2 && !wait_or_abort(&bars[4 + s], (eph >> s) & 1u, abort_flag, a.err)) break;
+        if (tid == 0) misc[4 + s] = kNoBatch;
+        mbar_arrive(&bars[2 + s]);
+        break;
+      }
       uint32_t t0, t1;
       batch_range(b, t0, t1);
       const uint32_t i0 = 3 * t0, n = 3 * (t1 - t0), base = i0 & ~3u, pad = i0 - base;
@@ -262,10 +272,17 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
       if (!wait_or_abort(&bars[s], (wph >> s) & 1u, abort_flag, a.err)) break;
       wph ^= 1u << s;
       window_pending = false;
-      if (tid == 0 && b + stride < nb) {
-        issue_window(b + stride, s ^ 1u);  // that window buffer was read before the last batch's barriers
-        window_pending = true;
-        pending_buf = s ^ 1u;
+      if (tid == 0) {
+        // claim the next batch; its window goes into the other buffer, which
+        // was read before the last batch's barrier
+        const uint32_t next = stride + atomicAdd(reinterpret_cast<unsigned int*>(a.counters + CNT_WORK), 1u);
+        misc[6 + (s ^ 1u)] = next;
+        misc[4 + s] = b;
+        if (next < nb) {
+          issue_window(next, s ^ 1u);
+          window_pending = true;
+          pending_buf = s ^ 1u;
+        }
       }
       if (n > a.max_batch_idx) {  // cannot happen with a consistent partition; uniform
         if (tid == 0) atomicOr(a.err, EBIT_CAPACITY);
@@ -451,8 +468,9 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
       cp_async_mbar_arrive(&bars[2 + s]);
       mbar_arrive(&bars[2 + s]);
       // every id of the batch inserted, the other table empty again; the
-      // window and the sort keys are free
+      // window and the sort keys are free; the next batch is known
       named_sync(kBarProducers, NP);
+      b = misc[6 + (s ^ 1u)];
     }
     // never leave a copy in flight into this block's shared memory
     cp_async_wait<0>();
@@ -466,11 +484,12 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
     unsigned long long inv_total = 0, nbatches = 0;
     bool bulk_pending = false;  // a bulk store of this warp may still read its staging area
     uint32_t fph = 0u;  // bit s: parity of full[s]
-    uint32_t j = 0;
-    for (uint32_t b = blockIdx.x; b < nb; b += stride, ++j) {
+    for (uint32_t j = 0;; ++j) {
       const uint32_t s = j & 1u;
       if (!wait_or_abort(&bars[2 + s], (fph >> s) & 1u, abort_flag, a.err)) break;
       fph ^= 1u << s;
+      const uint32_t b = misc[4 + s];  // the slot's batch
+      if (b == kNoBatch) break;
       uint32_t t0, t1;
       batch_range(b, t0, t1);
       const uint32_t i0 = 3 * t0, n = 3 * (t1 - t0), base = i0 & ~3u, pad = i0 - base;
