@@ -91,7 +91,7 @@ def envelope(pos, nrm, d, dirs):
 
 
 def load(pos, nrm, M, N, steps: int):
-    """Synthetic load (Section 4.2: "a load of 256, 512 and 1024 cycles").
+    """Synthetic load (Section 4.2: the simple shader plus a load of 256, 512 or 1024 cycles).
 
     The simple shader, with the normal scaled by sigma_L of the contractive
     recurrence sigma_0 = 1, sigma_{k+1} = sigma_k / 2 + c, c = 1/2 + p_x/1000
