@@ -744,8 +744,16 @@ def serving_section(gp, torch, args):
         gp.gp_server_destroy(srv)
         runs[key] = res
     gp.gp_destroy(ctx)
+    # the highest arrival rate the server holds with p99 latency under 2 ms
+    ok = [(int(lam), r) for lam, r in runs["rates"].items() if r["p99_ms"] < 2.0]
+    best = max(ok, key=lambda kv: kv[0]) if ok else None
+    summary = None
+    if best:
+        lam, r = best
+        summary = {"requests_per_s": lam, "triangles_per_s": r["triangles_per_s"], "p99_ms": r["p99_ms"],
+                   "hbm_frac_device": r["hbm_frac_device"], "hbm_frac": r["hbm_frac"]}
     return {"workload": f"Poisson requests over {len(pool)} resident meshes (50-200k triangles, MVP/skinning)",
-            "peak_kind": peak_kind, **runs}
+            "peak_kind": peak_kind, "best_under_2ms_p99": summary, **runs}
 
 
 def main():
@@ -978,6 +986,11 @@ def main():
         if args.workloads_out:
             with open(args.workloads_out, "w") as f:
                 json.dump({"headline": line, **detail}, f, indent=1)
+        if "serving" in detail and detail["serving"].get("best_under_2ms_p99"):
+            sv = detail["serving"]["best_under_2ms_p99"]
+            line["serving"] = {"max_rate_p99_under_2ms": sv["requests_per_s"],
+                               "triangles_per_s": round(sv["triangles_per_s"]), "p99_ms": round(sv["p99_ms"], 3),
+                               "hbm_frac_device": round(sv["hbm_frac_device"], 3)}
         if "heavy" in detail and "variants" in detail["heavy"]:
             hv = detail["heavy"]
             line["heavy"] = {"best": hv["best"], "best_vs_naive": round(hv["best_vs_naive"], 3),
