@@ -147,68 +147,71 @@ __device__ __forceinline__ void load_raw(const unsigned char* row, VertexIn& v) 
   }
 }
 
-// One compare-exchange of the bitonic network seen from element i holding x,
-// whose partner (i ^ j) holds y: ascending runs where (i & k) == 0; the lower
-// index of a pair keeps the smaller key in an ascending run.
-template <class T>
-__device__ __forceinline__ T bitonic_keep(T x, T y, uint32_t i, uint32_t j, uint32_t k) {
-  const bool asc = (i & k) == 0;
-  const bool lower = (i & j) == 0;
-  const bool take_min = lower == asc;
-  const T mn = x < y ? x : y, mx = x < y ? y : x;
-  return take_min ? mn : mx;
-}
-
 // Bitonic network over N = E * NT keys with E consecutive keys per thread
 // in registers: stages with j < E stay in the thread, E <= j < 32 E exchange
 // within the warp by shuffles (partner lane = lane ^ j/E), and only
-// j >= 32 E goes through shared memory.
+// j >= 32 E goes through shared memory.  For k >= E a thread's E keys all
+// lie in one run (ascending where (E tid) & k == 0), and for j >= E they are
+// all on the same side of their pairs, so direction and side are worked out
+// once per stage; each exchange is then a min or a max.
 template <int E, class T, class Sync>
 __device__ __forceinline__ void bitonic_sort_regs(T* keys, uint32_t N, uint32_t tid, Sync sync) {
   T r[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) r[e] = keys[E * tid + e];
+  const uint32_t i0 = E * tid;  // this thread's first key
   for (uint32_t k = 2; k <= N; k <<= 1) {
+    const bool asc = (i0 & k) == 0;  // the thread's run (k >= E)
     for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      if (j >= 32u * E) {
-        sync();  // every thread has read the previous contents
+      if (j >= (uint32_t)E) {
+        const bool take_min = ((i0 & j) == 0) == asc;  // lower side of an ascending pair, or upper of a descending
+        if (j >= 32u * E) {
+          sync();  // every thread has read the previous contents
 #pragma unroll
-        for (int e = 0; e < E; ++e) keys[E * tid + e] = r[e];
-        sync();
+          for (int e = 0; e < E; ++e) keys[i0 + e] = r[e];
+          sync();
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const uint32_t i = E * tid + e;
-          r[e] = bitonic_keep(r[e], keys[i ^ j], i, j, k);
-        }
-      } else if (j >= (uint32_t)E) {
-        const uint32_t lm = j / E;
+          for (int e = 0; e < E; ++e) {
+            const T y = keys[(i0 + e) ^ j];
+            r[e] = take_min ? (r[e] < y ? r[e] : y) : (r[e] < y ? y : r[e]);
+          }
+        } else {
+          const uint32_t lm = j / E;
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const T y = __shfl_xor_sync(kFull, r[e], lm);
-          r[e] = bitonic_keep(r[e], y, E * tid + e, j, k);
+          for (int e = 0; e < E; ++e) {
+            const T y = __shfl_xor_sync(kFull, r[e], lm);
+            r[e] = take_min ? (r[e] < y ? r[e] : y) : (r[e] < y ? y : r[e]);
+          }
         }
       } else {
-        // j < E: the partner is in this thread (j is 1, 2 or 4, each with
-        // compile-time register indices)
-        T q[E];
+        // j < E: both keys of a pair are in this thread (j is 1, 2 or 4, each
+        // with compile-time register indices); the lower one keeps the
+        // smaller key in an ascending run
+        auto exch = [&](int lo, int hi) {
+          const bool up = k >= (uint32_t)E ? asc : ((i0 + lo) & k) == 0;
+          const T a = r[lo], b = r[hi];
+          const T mn = a < b ? a : b, mx = a < b ? b : a;
+          r[lo] = up ? mn : mx;
+          r[hi] = up ? mx : mn;
+        };
         if (j == 1) {
 #pragma unroll
-          for (int e = 0; e < E; ++e) q[e] = bitonic_keep(r[e], r[e ^ 1], E * tid + e, 1u, k);
+          for (int e = 0; e < E; e += 2) exch(e, e + 1);
         } else if (j == 2) {
 #pragma unroll
-          for (int e = 0; e < E; ++e) q[e] = bitonic_keep(r[e], r[e ^ 2], E * tid + e, 2u, k);
+          for (int e = 0; e < E; ++e)
+            if ((e & 2) == 0) exch(e, e + 2);
         } else {
 #pragma unroll
-          for (int e = 0; e < E; ++e) q[e] = bitonic_keep(r[e], r[(e ^ 4) & (E - 1)], E * tid + e, 4u, k);
+          for (int e = 0; e < E; ++e)
+            if ((e & 4) == 0 && e + 4 < E) exch(e, e + 4);
         }
-#pragma unroll
-        for (int e = 0; e < E; ++e) r[e] = q[e];
       }
     }
   }
   sync();
 #pragma unroll
-  for (int e = 0; e < E; ++e) keys[E * tid + e] = r[e];
+  for (int e = 0; e < E; ++e) keys[i0 + e] = r[e];
   sync();
 }
 
