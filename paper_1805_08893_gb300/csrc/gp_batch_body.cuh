@@ -154,11 +154,11 @@ __device__ __forceinline__ void load_raw(const unsigned char* row, VertexIn& v) 
 // lie in one run (ascending where (E tid) & k == 0), and for j >= E they are
 // all on the same side of their pairs, so direction and side are worked out
 // once per stage; each exchange is then a min or a max.
+// The network on keys already in registers (r: keys E tid .. E tid + E - 1);
+// the shared-memory stages use keys[0..N) as their exchange buffer.  Leaves
+// the sorted keys in r.
 template <int E, class T, class Sync>
-__device__ __forceinline__ void bitonic_sort_regs(T* keys, uint32_t N, uint32_t tid, Sync sync) {
-  T r[E];
-#pragma unroll
-  for (int e = 0; e < E; ++e) r[e] = keys[E * tid + e];
+__device__ __forceinline__ void bitonic_network_regs(T (&r)[E], T* keys, uint32_t N, uint32_t tid, Sync sync) {
   const uint32_t i0 = E * tid;  // this thread's first key
   for (uint32_t k = 2; k <= N; k <<= 1) {
     const bool asc = (i0 & k) == 0;  // the thread's run (k >= E)
@@ -209,9 +209,19 @@ __device__ __forceinline__ void bitonic_sort_regs(T* keys, uint32_t N, uint32_t 
       }
     }
   }
+}
+
+// The register network on keys[0..N), N = E NT: loads each thread's E keys,
+// sorts, and stores them back.
+template <int E, class T, class Sync>
+__device__ __forceinline__ void bitonic_sort_regs(T* keys, uint32_t N, uint32_t tid, Sync sync) {
+  T r[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) r[e] = keys[E * tid + e];
+  bitonic_network_regs<E>(r, keys, N, tid, sync);
   sync();
 #pragma unroll
-  for (int e = 0; e < E; ++e) keys[i0 + e] = r[e];
+  for (int e = 0; e < E; ++e) keys[E * tid + e] = r[e];
   sync();
 }
 
@@ -255,10 +265,79 @@ __device__ __forceinline__ void bitonic_sort(T* keys, uint32_t N, uint32_t tid, 
 // stay below 2^(32 - pb) - 1, the id field's largest value standing for an
 // id out of range (the host picks 32-bit keys when the vertex count allows
 // it: half the registers and shuffles of the sorting network).
+// With N = E NT (E = 4 or 8) every step runs on registers: each thread
+// builds its E consecutive keys, the network sorts them in place, and the
+// thread flags, ranks and scatters the same E keys -- no pass of the keys
+// through shared memory but the network's own exchange stages.
+template <int E, class T, class Sync, class Consume>
+__device__ __forceinline__ void sort_dedup_regs(const DrawArgs& a, const BatchSmem& S, const uint32_t* ids,
+                                                uint32_t n, uint32_t tid, uint32_t NT, Sync sync,
+                                                const Consume& consume, uint32_t pb) {
+  const uint32_t lane = lane_id(), warp = tid >> 5, i0 = E * tid;
+  T* keys = reinterpret_cast<T*>(S.keys);
+  const T invalid = (T)((sizeof(T) == 4 ? (1ull << (32 - pb)) - 1 : (unsigned long long)kInvalidId));
+  auto id_of = [&](T key) { return (uint32_t)(key >> pb); };
+  T r[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint32_t i = i0 + e;
+    const uint32_t id = i < n ? ids[i] : 0u;
+    r[e] = i < n ? (((id < a.num_verts ? (T)id : invalid) << pb) | (T)i) : ~(T)0;
+  }
+  bitonic_network_regs<E>(r, keys, E * NT, tid, sync);
+  // the key after this thread's last one: the next lane's first, or for
+  // lane 31 the next warp's first, passed through shared memory
+  sync();  // every thread has read the network's last shared-memory stage
+  if (lane == 0) keys[i0] = r[0];
+  sync();
+  T after = __shfl_down_sync(kFull, r[0], 1);
+  if (lane == 31) after = tid + 1 < NT ? keys[i0 + E] : ~(T)0;
+  // tail flags (the last key of each id's group), then a group scan
+  uint32_t tails = 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const T next = e + 1 < E ? r[e + 1 < E ? e + 1 : e] : after;
+    const uint32_t i = i0 + e;
+    if (i < n && (i == n - 1 || id_of(r[e]) != id_of(next))) tails |= 1u << e;
+  }
+  const uint32_t cnt = __popc(tails);
+  const uint32_t inc = warp_inclusive_scan(cnt);
+  if (lane == 31) S.wsum[warp] = inc;
+  sync();
+  uint32_t rk = inc - cnt;
+  for (uint32_t w = 0; w < warp; ++w) rk += S.wsum[w];
+  if (tid == NT - 1) *S.ucount = rk + cnt;
+  const uint32_t rb = __shfl_sync(kFull, rk, 0), re = __shfl_sync(kFull, rk + cnt, 31);
+  const T pmask = (T)((1ull << (sizeof(T) == 4 ? pb : 16)) - 1);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    if (i0 + e < n) {
+      S.map[(uint32_t)(r[e] & pmask)] = (uint16_t)rk;
+      if ((tails >> e) & 1u) {
+        const uint32_t id = id_of(r[e]);
+        if (rk < a.ucap) S.uniq[rk] = (T)id == invalid ? kInvalidId : id;
+        else atomicOr(a.err, EBIT_CAPACITY);
+        ++rk;
+      }
+    }
+  }
+  __syncwarp();
+  consume(rb, re, lane);
+  __syncwarp();
+}
+
 template <class T, class Sync, class Consume>
 __device__ __forceinline__ void sort_dedup(const DrawArgs& a, const BatchSmem& S, const uint32_t* ids, uint32_t n,
                                            uint32_t tid, uint32_t NT, Sync sync, const Consume& consume,
                                            uint32_t pb) {
+  if (a.sort_n == 8 * NT) {
+    sort_dedup_regs<8, T>(a, S, ids, n, tid, NT, sync, consume, pb);
+    return;
+  }
+  if (a.sort_n == 4 * NT) {
+    sort_dedup_regs<4, T>(a, S, ids, n, tid, NT, sync, consume, pb);
+    return;
+  }
   const uint32_t lane = lane_id(), warp = tid >> 5;
   T* keys = reinterpret_cast<T*>(S.keys);
   const T invalid = (T)((sizeof(T) == 4 ? (1ull << (32 - pb)) - 1 : (unsigned long long)kInvalidId));
