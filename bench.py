@@ -70,6 +70,14 @@ def parse_args():
     return ap.parse_args()
 
 
+# Dynamic-batch limits for hash/phash, tuned to the reuse kernel: one
+# producer pass of a 256-thread block (5 warps x 32 lanes x 8 positions)
+# covers 1280 indices, so batches of up to 426 triangles (1278 indices) fill
+# it; a 2048-slot table keeps the load at <= 320 unique ids low.  The paper's
+# own limits (1023 indices, 256 unique: the library's defaults) are timed as
+# hash_dynamic_1023; sort keeps them (1024 keys: 8 per producer thread).
+TUNED = {"max_unique": 320, "max_tris": 426, "hash_slots": 2048}
+
 # (name, variant, mode, extra config)
 VARIANTS = [
     ("naive", "naive", "static", {}),
@@ -79,8 +87,9 @@ VARIANTS = [
     ("hash_static_s768", "hash", "static", {"batch_indices": 768}),
     ("phash_static_s768", "phash", "static", {"batch_indices": 768}),
     ("sort_dynamic", "sort", "dynamic", {}),
-    ("hash_dynamic", "hash", "dynamic", {}),
-    ("phash_dynamic", "phash", "dynamic", {}),
+    ("hash_dynamic_1023", "hash", "dynamic", {}),
+    ("phash_dynamic", "phash", "dynamic", TUNED),
+    ("hash_dynamic", "hash", "dynamic", TUNED),
 ]
 
 
@@ -95,7 +104,7 @@ def load_peaks():
 
 def dram_traffic_record():
     """ncu DRAM bytes per launch of the headline kernel, if the committed
-    profile summary matches the current kernel source."""
+    profile summary matches the current kernel source and batch limits."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         rec = json.load(open(p))
@@ -105,7 +114,7 @@ def dram_traffic_record():
         h = sources_sha256(rec.get("sources", []))
     except Exception:
         return None
-    if not rec.get("sources") or h != rec.get("sources_sha256"):
+    if not rec.get("sources") or h != rec.get("sources_sha256") or rec.get("config") != TUNED:
         return None
     return rec
 
@@ -267,7 +276,8 @@ def headline_config(f, world):
     V, T = 10 * f * f + 2, 20 * f * f
     return {"workload": f"large scanned-style mesh: geodesic sphere f={f}, {V} vertices / {T} triangles, "
                         f"Morton order + 5% block shuffle, permuted vertex ids, MVP+normal shader",
-            "variant": HEADLINE, "max_unique": 256, "max_tris": 341, "threads_per_group": 256,
+            "variant": HEADLINE, "max_unique": TUNED["max_unique"], "max_tris": TUNED["max_tris"],
+            "hash_slots": TUNED["hash_slots"], "threads_per_group": 256,
             "segment_tris": 4096, "parallelism": "replicas" if world > 1 else "single GPU",
             "l2": "inputs (201 MB) and output (605 MB) exceed the 126 MB L2; no flush"}
 
@@ -356,7 +366,7 @@ def heavy_section(gp, torch, args):
     props = torch.cuda.get_device_properties(0)
     res = {}
     for name, variant, mode, extra in [("naive", "naive", 0, {}), ("multi", "multi", 0, {}), ("warp_s96", "warp", 0, {}),
-                                       ("hash_dynamic", "hash", 1, {}), ("phash_dynamic", "phash", 1, {}),
+                                       ("hash_dynamic", "hash", 1, TUNED), ("phash_dynamic", "phash", 1, TUNED),
                                        ("sort_dynamic", "sort", 1, {}), ("hash_static_s768", "hash", 0,
                                                                          {"batch_indices": 768})]:
         ctx = gp.gp_create(variant, mode=mode, stream=stream, **extra)
@@ -397,6 +407,8 @@ def table2_section(gp, torch, args):
     verts = torch.from_numpy(mesh.vertices).cuda()
     out = torch.empty(T * 21, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
+    # the paper's dynamic limits for this table (1023 indices, 256 unique): at
+    # the heavy loads the larger tuned batches give each consumer more to shade
     methods = [("naive", "naive", 0, {}), ("warp", "warp", 0, {"batch_indices": 96}), ("hash", "hash", 1, {}),
                ("phash", "phash", 1, {}), ("sort", "sort", 1, {}), ("multi", "multi", 0, {})]
     ctxs = []
@@ -891,7 +903,7 @@ def main():
         hidx = torch.from_numpy(mesh.indices.view(np.int32)).pin_memory()
         hvert = torch.from_numpy(mesh.vertices).pin_memory()
         hout = torch.empty(T * 21, dtype=torch.float32).pin_memory()
-        ectx = gp.gp_create("hash", mode=gp.GP_BATCH_DYNAMIC, stream=stream)
+        ectx = gp.gp_create("hash", mode=gp.GP_BATCH_DYNAMIC, stream=stream, **TUNED)
         ksteps = max(1, min(args.steps, 10))
         for _ in range(2):
             gp.gp_draw_host(ectx, hidx, hvert, gp.GP_SHADER_MVP, uni, hout)

@@ -1,6 +1,8 @@
 """Parity at the benchmark's full size: the 7.2M-triangle geodesic sphere
-(f = 600) in the launch configuration bench.py times (dynamic batches of 256
-unique / 341 triangles, 256 threads, segments of 4096 triangles).
+(f = 600) in the launch configurations bench.py times (256 threads, segments
+of 4096 triangles; dynamic batches of <= 320 unique / 426 triangles with a
+2048-slot table for hash and phash, and of <= 256 unique / 341 triangles,
+the paper's limits, for sort and for hash beside them).
 
 Exact: the partition against the oracle's front-to-back scan, the vertex
 behind every one of the 21.6M corners, and every batch's invocation count.
@@ -18,18 +20,29 @@ from helpers_gp import assert_attrs_close, draw_gpu, uniforms_for
 pytestmark = pytest.mark.gpu
 
 
+# the dynamic-batch configurations bench.py draws with
+TUNED = {"max_unique": 320, "max_tris": 426, "hash_slots": 2048}
+PAPER = {"max_unique": 256, "max_tris": 341}
+BENCH_DYNAMIC = [("hash", TUNED), ("phash", TUNED), ("sort", PAPER), ("hash", PAPER)]
+
+
+def _partitions(mesh):
+    return {(c["max_unique"], c["max_tris"]): B.dynamic_partition(mesh.indices, c["max_unique"], c["max_tris"], 4096)
+            for c in (TUNED, PAPER)}
+
+
 @pytest.fixture(scope="module")
 def big():
     mesh = mg.geodesic_sphere(600, 2)
-    starts = B.dynamic_partition(mesh.indices, 256, 341, 4096)
-    return mesh, starts
+    return mesh, _partitions(mesh)
 
 
-@pytest.mark.parametrize("variant", ["hash", "phash", "sort"])
-def test_full_size_dynamic(big, variant):
-    mesh, starts = big
+@pytest.mark.parametrize("variant,cfg", BENCH_DYNAMIC, ids=["hash", "phash", "sort", "hash-1023"])
+def test_full_size_dynamic(big, variant, cfg):
+    mesh, parts = big
+    starts = parts[(cfg["max_unique"], cfg["max_tris"])]
     uni, uni_o = uniforms_for(mesh, S.SHADER_MVP, seed=2)
-    r = draw_gpu(mesh, variant, S.SHADER_MVP, "dynamic", uni, threads_per_group=256)
+    r = draw_gpu(mesh, variant, S.SHADER_MVP, "dynamic", uni, threads_per_group=256, **cfg)
     assert r.status == 0
     assert r.starts.tolist() == starts
     assert np.array_equal(r.ids, mesh.indices)
@@ -60,15 +73,15 @@ def test_full_size_baselines(big, variant):
 @pytest.fixture(scope="module")
 def heavy():
     mesh = mg.geodesic_sphere(316, 4)
-    starts = B.dynamic_partition(mesh.indices, 256, 341, 4096)
-    return mesh, starts
+    return mesh, _partitions(mesh)
 
 
-@pytest.mark.parametrize("variant", ["hash", "phash", "sort"])
-def test_envelope_bench_size_dynamic(heavy, variant):
-    mesh, starts = heavy
+@pytest.mark.parametrize("variant,cfg", BENCH_DYNAMIC[:3], ids=["hash", "phash", "sort"])
+def test_envelope_bench_size_dynamic(heavy, variant, cfg):
+    mesh, parts = heavy
+    starts = parts[(cfg["max_unique"], cfg["max_tris"])]
     uni, uni_o = uniforms_for(mesh, S.SHADER_ENVELOPE)
-    r = draw_gpu(mesh, variant, S.SHADER_ENVELOPE, "dynamic", uni, threads_per_group=256)
+    r = draw_gpu(mesh, variant, S.SHADER_ENVELOPE, "dynamic", uni, threads_per_group=256, **cfg)
     assert r.status == 0
     assert r.starts.tolist() == starts
     assert np.array_equal(r.ids, mesh.indices)
