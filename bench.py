@@ -927,6 +927,8 @@ def main():
     bytes_inv = 12 * T + 32 * inv + 84 * T
     achieved = bytes_inv / (kernel_ms * 1e-3) / 1e9
     traffic = dram_traffic_record()
+    if traffic and traffic.get("full_launch_tris") != T:  # the record is for the f=600 launch only
+        traffic = None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_kind": f"of {peak_kind}", "traffic": traffic["bytes_per_launch"] if traffic else None,
                 "algorithmic_bytes_per_launch": bytes_inv,
