@@ -74,7 +74,8 @@ __host__ __device__ inline ReuseLayout reuse_layout(int dedup, int shader, const
   uint32_t o = 0;
   L.off_bar = o; o += 64;       // window[2], full[2], empty[2]
   L.off_misc = o; o += 64 * 4;  // [0], [1]: unique counters of the two slots; [2]: abort; [4], [5]: each slot's
-                                // batch; [6], [7]: the producers' next batch; [8..]: sort scan
+                                // batch; [6], [7]: the producers' next batch; [8..31]: sort scan; [32..35]: first
+                                // and end triangle of the batch in each window buffer; [36..39]: of each slot's batch
   L.groups = (a.max_batch_idx + 6) / 4;  // pad (<= 3) + indices, in 4-word groups
   L.win_words = 4 * L.groups;
   L.off_win = o; o += 2 * L.win_words * 4;
@@ -221,19 +222,23 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
   // Thread 0: bulk copy of the 16-byte-aligned superset of batch b's window,
   // clipped to the 16-byte-granular part of the buffer (the rest is loaded
   // by plain loads).  A window larger than the buffer is refused here and
-  // flagged by the producers.
-  auto issue_window = [&](uint32_t b, uint32_t buf) {
+  // flagged by the producers.  The batch's triangle range goes beside it in
+  // shared memory, so that no producer waits on a global load for it.
+  auto issue_window = [&](uint32_t b, uint32_t buf, bool copy) {
     uint32_t t0, t1;
     batch_range(b, t0, t1);
+    misc[32 + 2 * buf] = t0;
+    misc[33 + 2 * buf] = t1;
     const uint32_t base = (3 * t0) & ~3u, end = min((3 * t1 + 3) & ~3u, n4);
     const uint32_t bytes = (end > base && end - base <= L.win_words) ? (end - base) * 4 : 0;
+    if (!copy) {  // failure injection: bytes that never come
+      mbar_arrive_expect_tx(&bars[buf], 16);
+      return;
+    }
     mbar_arrive_expect_tx(&bars[buf], bytes);
     if (bytes) bulk_load(winbuf + buf * L.win_words, a.idx + base, bytes, &bars[buf]);
   };
-  if (tid == 0) {
-    if (a.test_stall) mbar_arrive_expect_tx(&bars[0], 16);  // failure injection: bytes that never come
-    else issue_window(blockIdx.x, 0);
-  }
+  if (tid == 0) issue_window(blockIdx.x, 0, !a.test_stall);
   __syncthreads();
   const uint32_t stride = gridDim.x;
 
@@ -253,8 +258,7 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
         mbar_arrive(&bars[2 + s]);
         break;
       }
-      uint32_t t0, t1;
-      batch_range(b, t0, t1);
+      const uint32_t t0 = misc[32 + 2 * s], t1 = misc[33 + 2 * s];  // left by thread 0 with the window
       const uint32_t i0 = 3 * t0, n = 3 * (t1 - t0), base = i0 & ~3u, pad = i0 - base;
       const uint32_t ngroups = (pad + n + 3) >> 2;
       unsigned char* slot_p = ring(s);
@@ -278,8 +282,10 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
         const uint32_t next = stride + atomicAdd(reinterpret_cast<unsigned int*>(a.counters + CNT_WORK), 1u);
         misc[6 + (s ^ 1u)] = next;
         misc[4 + s] = b;
+        misc[36 + 2 * s] = t0;  // the slot's batch, for the consumers
+        misc[37 + 2 * s] = t1;
         if (next < nb) {
-          issue_window(next, s ^ 1u);
+          issue_window(next, s ^ 1u, true);
           window_pending = true;
           pending_buf = s ^ 1u;
         }
@@ -298,14 +304,6 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
         }
       }
       uint32_t* tbl = table + (DEDUP == DEDUP_SORT ? 0u : s * a.hash_slots);  // this batch's hash table
-      if (DEDUP != DEDUP_SORT) {
-        // empty the other table for the next batch (the last batch used it;
-        // the barrier at the end of this batch orders the clear before the
-        // next batch's insertions)
-        uint32_t* other = table + (s ^ 1u) * a.hash_slots;
-        for (uint32_t sl = 4 * tid; sl < a.hash_slots; sl += 4 * NP)
-          *reinterpret_cast<uint4*>(other + sl) = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
-      }
       if (DEDUP == DEDUP_SORT) {
         BatchSmem S;
         S.map = map + pad;
@@ -467,6 +465,14 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
       // arrived and this thread's row copies have landed
       cp_async_mbar_arrive(&bars[2 + s]);
       mbar_arrive(&bars[2 + s]);
+      if (DEDUP != DEDUP_SORT) {
+        // empty the other table for the next batch (the last batch used it),
+        // after this batch's insertions so that the stores do not queue
+        // ahead of its atomics
+        uint32_t* other = table + (s ^ 1u) * a.hash_slots;
+        for (uint32_t sl = 4 * tid; sl < a.hash_slots; sl += 4 * NP)
+          *reinterpret_cast<uint4*>(other + sl) = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+      }
       // every id of the batch inserted, the other table empty again; the
       // window and the sort keys are free; the next batch is known
       named_sync(kBarProducers, NP);
@@ -490,8 +496,7 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
       fph ^= 1u << s;
       const uint32_t b = misc[4 + s];  // the slot's batch
       if (b == kNoBatch) break;
-      uint32_t t0, t1;
-      batch_range(b, t0, t1);
+      const uint32_t t0 = misc[36 + 2 * s], t1 = misc[37 + 2 * s];
       const uint32_t i0 = 3 * t0, n = 3 * (t1 - t0), base = i0 & ~3u, pad = i0 - base;
       const uint32_t ngroups = (pad + n + 3) >> 2;
       unsigned char* slot_p = ring(s);
