@@ -2,10 +2,10 @@
 // parallel hashing (Section 3.4), over static batches (Section 3.3) or the
 // dynamic batches of the partition (Section 3.4).
 //
-// Each block is persistent (grid = SMs x resident blocks): it starts with
-// batch blockIdx.x and then claims batches gridDim.x, gridDim.x + 1, ...
-// from a per-draw counter, one at a time, so blocks that run faster take
-// more batches and all finish together.  Its warps have two roles
+// Each block is persistent (grid = SMs x resident blocks): it takes batches
+// blockIdx.x, blockIdx.x + gridDim.x, ... in turn, and for the last few
+// rounds of the draw claims batches from a per-draw counter, one at a time,
+// so blocks that run faster take more of them and all finish together.  Its warps have two roles
 // that run side by side, handing batches over through a two-deep ring of
 // shared-memory slots guarded by mbarriers ("full": deduplicated, rows
 // landed; "empty": assembled, slot free):
@@ -44,6 +44,7 @@
 namespace gp {
 
 constexpr uint32_t kNoBatch = 0xFFFFFFFFu;  // a ring slot that ends the block's work
+constexpr uint32_t kDynamicRounds = 6;       // rounds of batches per block claimed from the counter
 constexpr uint32_t kBarProducers = 1;  // named barrier of the producer warps
 constexpr uint32_t kBarConsumers = 2;  // named barrier of the consumer warps
 
@@ -224,9 +225,7 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
   // by plain loads).  A window larger than the buffer is refused here and
   // flagged by the producers.  The batch's triangle range goes beside it in
   // shared memory, so that no producer waits on a global load for it.
-  auto issue_window = [&](uint32_t b, uint32_t buf, bool copy) {
-    uint32_t t0, t1;
-    batch_range(b, t0, t1);
+  auto issue_window = [&](uint32_t t0, uint32_t t1, uint32_t buf, bool copy) {
     misc[32 + 2 * buf] = t0;
     misc[33 + 2 * buf] = t1;
     const uint32_t base = (3 * t0) & ~3u, end = min((3 * t1 + 3) & ~3u, n4);
@@ -238,9 +237,18 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
     mbar_arrive_expect_tx(&bars[buf], bytes);
     if (bytes) bulk_load(winbuf + buf * L.win_words, a.idx + base, bytes, &bars[buf]);
   };
-  if (tid == 0) issue_window(blockIdx.x, 0, !a.test_stall);
+  if (tid == 0) {
+    uint32_t t0, t1;
+    batch_range(blockIdx.x, t0, t1);
+    issue_window(t0, t1, 0, !a.test_stall);
+  }
   __syncthreads();
-  const uint32_t stride = gridDim.x;
+  // batches [0, nstatic) go to the blocks in turn (block i: i, i + grid,
+  // ...); the last rounds, from nstatic on, are claimed from the per-draw
+  // counter, so blocks that run faster take more of them and all finish
+  // together -- and the claim's global atomic stays out of most batches
+  const uint32_t G = gridDim.x;
+  const uint32_t nstatic = G * max(1u, nb / G > kDynamicRounds ? nb / G - kDynamicRounds : 1u);
 
   if (warp < NPW) {
     // ======================= producers =======================
@@ -251,7 +259,7 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
     uint32_t b = blockIdx.x;  // the batch this iteration deduplicates
     for (uint32_t j = 0;; ++j) {
       const uint32_t s = j & 1u;
-      if (*abort_flag) break;
+      // (a block stopped by another thread is noticed in the waits below)
       if (b >= nb) {  // no batch left: hand the consumers a slot that says so
         if (j >= 2 && !wait_or_abort(&bars[4 + s], (eph >> s) & 1u, abort_flag, a.err)) break;
         if (tid == 0) misc[4 + s] = kNoBatch;
@@ -277,15 +285,18 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
       wph ^= 1u << s;
       window_pending = false;
       if (tid == 0) {
-        // claim the next batch; its window goes into the other buffer, which
-        // was read before the last batch's barrier
-        const uint32_t next = stride + atomicAdd(reinterpret_cast<unsigned int*>(a.counters + CNT_WORK), 1u);
+        // the next batch's window goes into the other buffer, which was read
+        // before the last batch's barrier
+        const uint32_t next =
+            b + G < nstatic ? b + G : nstatic + atomicAdd(reinterpret_cast<unsigned int*>(a.counters + CNT_WORK), 1u);
         misc[6 + (s ^ 1u)] = next;
         misc[4 + s] = b;
         misc[36 + 2 * s] = t0;  // the slot's batch, for the consumers
         misc[37 + 2 * s] = t1;
         if (next < nb) {
-          issue_window(next, s ^ 1u, true);
+          uint32_t nt0, nt1;
+          batch_range(next, nt0, nt1);
+          issue_window(nt0, nt1, s ^ 1u, true);
           window_pending = true;
           pending_buf = s ^ 1u;
         }
