@@ -13,7 +13,7 @@ baseline are measured on the same mesh and reported under "variants".
 
 Prints one JSON line on stdout (rank 0), the last thing it prints: the
 headline.  The extra workloads (heavy shader, Table 2 rows, frame, serving,
-Table 1, random walk, Loop subdivision) go to stderr as "[workload] {...}"
+Table 1, random walk, Loop subdivision) and every variant's figures go to stderr as "[workload] {...}"
 lines and, with --workloads-out, to a JSON file.  --impl reference times
 the CPU oracle (the plain definition of the result) on a bounded sample
 instead.
@@ -1013,6 +1013,10 @@ def main():
             "clocks": clocks,
         }
         detail = {"variants": results, "mesh_gen_s": gen_s}
+        print("[workload] " + json.dumps({"section": "variants", "workload": line["config"]["workload"],
+                                          "variants": {k: {kk: vv for kk, vv in v.items() if not isinstance(vv, dict)}
+                                                       for k, v in results.items()}}),
+              file=sys.stderr, flush=True)
         sections = [] if args.sections == "none" else [x for x in args.sections.split(",") if x]
         if world == 1 and sections:
             # release the headline mesh before the extra workloads
