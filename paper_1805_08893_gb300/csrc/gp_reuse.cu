@@ -5,13 +5,14 @@
 // Each block is persistent (grid = SMs x resident blocks): it takes batches
 // blockIdx.x, blockIdx.x + gridDim.x, ... in turn, and for the last few
 // rounds of the draw claims batches from a per-draw counter, one at a time,
-// so blocks that run faster take more of them and all finish together.  Its warps have two roles
-// that run side by side, handing batches over through a two-deep ring of
-// shared-memory slots guarded by mbarriers ("full": deduplicated, rows
-// landed; "empty": assembled, slot free):
+// so blocks that run faster take more of them and all finish together.
+// Its warps have two roles that run side by side, handing batches over
+// through a two-deep ring of shared-memory slots guarded by mbarriers
+// ("full": deduplicated, rows landed; "empty": assembled, slot free):
 //
-//   producer warps (the first half) deduplicate batch j into slot j mod 2:
-//     the index window (bulk-copied on an mbarrier one batch ahead) is read
+//   producer warps (five eighths of the block; sort: half) deduplicate
+//     batch j into slot j mod 2: the index window (bulk-copied on an
+//     mbarrier one batch ahead, its triangle range left beside it) is read
 //     from the 16-byte boundary at or below the batch's first index, 4 words
 //     per thread ("a group"); hash/phash -- each position's id is inserted
 //     into the shared open-addressing table with atomicCAS (multiplicative
@@ -25,7 +26,7 @@
 //     created.  Each group's 4 slots (hash) or ranks (sort) go to the map as
 //     u16 x 4.  The "full" mbarrier completes when every producer thread has
 //     arrived and every row copy has landed.
-//   consumer warps (the second half) take batch j from its slot: each unique
+//   consumer warps (the rest) take batch j from its slot: each unique
 //     vertex is shaded once, in place in its row; then every warp assembles
 //     its groups (4 corners' shaded rows per lane) through a per-warp staging
 //     area (a transpose): with 7 floats per corner a span that lies inside
