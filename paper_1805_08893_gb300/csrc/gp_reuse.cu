@@ -391,52 +391,60 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
             pend = probing;
           }
           if (DEDUP == DEDUP_PHASH) {
-            // the positions still pending, one at a time, probed by the whole
-            // warp 32 consecutive slots at a time
+            // the positions still pending (rare), one at a time -- the lowest
+            // lane's lowest position first -- probed by the whole warp 32
+            // consecutive slots at a time; one loop for all Q positions keeps
+            // this cold path small
+            for (uint32_t anyp = __ballot_sync(kFull, pend != 0u); anyp; anyp = __ballot_sync(kFull, pend != 0u)) {
+              const uint32_t leader = __ffs(anyp) - 1;
+              const uint32_t q = __ffs(__shfl_sync(kFull, pend, leader)) - 1;  // uniform
+              uint32_t myid = id[0], mysl = sl[0];
 #pragma unroll
-            for (int q = 0; q < Q; ++q) {
-              uint32_t left = __ballot_sync(kFull, (pend >> q) & 1u);
-              while (left) {
-                const uint32_t leader = __ffs(left) - 1;
-                const uint32_t lid = __shfl_sync(kFull, id[q], leader);
-                uint32_t lh = __shfl_sync(kFull, sl[q], leader);
-                uint32_t found = 0;
-                bool fresh = false;
-                for (uint32_t guard = 0;; ++guard) {
-                  if (guard > a.hash_slots / 16 + 64) {  // table full: cannot happen within capacity
-                    if (lane == 0) atomicOr(a.err, EBIT_CAPACITY);
-                    found = 0;
+              for (int k = 1; k < Q; ++k)
+                if (q == (uint32_t)k) {
+                  myid = id[k];
+                  mysl = sl[k];
+                }
+              const uint32_t lid = __shfl_sync(kFull, myid, leader);
+              uint32_t lh = __shfl_sync(kFull, mysl, leader);
+              uint32_t found = 0;
+              bool fresh = false;
+              for (uint32_t guard = 0;; ++guard) {
+                if (guard > a.hash_slots / 16 + 64) {  // table full: cannot happen within capacity
+                  if (lane == 0) atomicOr(a.err, EBIT_CAPACITY);
+                  found = 0;
+                  break;
+                }
+                const uint32_t ps = (lh + lane) & mask;
+                const uint32_t val = tbl[ps];
+                const uint32_t hit = __ballot_sync(kFull, val == lid);
+                if (hit) {
+                  found = (lh + __ffs(hit) - 1) & mask;
+                  break;
+                }
+                const uint32_t emp = __ballot_sync(kFull, val == kEmpty);
+                if (emp) {
+                  const uint32_t fl = __ffs(emp) - 1;
+                  const uint32_t cs = (lh + fl) & mask;
+                  uint32_t cv = 0;
+                  if (lane == fl) cv = atomicCAS(&tbl[cs], kEmpty, lid);
+                  cv = __shfl_sync(kFull, cv, fl);
+                  if (cv == kEmpty || cv == lid) {
+                    found = cs;
+                    fresh = cv == kEmpty;
                     break;
                   }
-                  const uint32_t ps = (lh + lane) & mask;
-                  const uint32_t val = tbl[ps];
-                  const uint32_t hit = __ballot_sync(kFull, val == lid);
-                  if (hit) {
-                    found = (lh + __ffs(hit) - 1) & mask;
-                    break;
-                  }
-                  const uint32_t emp = __ballot_sync(kFull, val == kEmpty);
-                  if (emp) {
-                    const uint32_t fl = __ffs(emp) - 1;
-                    const uint32_t cs = (lh + fl) & mask;
-                    uint32_t cv = 0;
-                    if (lane == fl) cv = atomicCAS(&tbl[cs], kEmpty, lid);
-                    cv = __shfl_sync(kFull, cv, fl);
-                    if (cv == kEmpty || cv == lid) {
-                      found = cs;
-                      fresh = cv == kEmpty;
-                      break;
-                    }
-                    lh = cs;  // the slot was just taken: probe on from it
-                  } else {
-                    lh = (lh + 32) & mask;
-                  }
+                  lh = cs;  // the slot was just taken: probe on from it
+                } else {
+                  lh = (lh + 32) & mask;
                 }
-                if (lane == leader) {
-                  sl[q] = found;
-                  newmask |= (fresh ? 1u : 0u) << q;
-                }
-                left &= left - 1;
+              }
+              if (lane == leader) {
+#pragma unroll
+                for (int k = 0; k < Q; ++k)
+                  if (q == (uint32_t)k) sl[k] = found;
+                newmask |= (fresh ? 1u : 0u) << q;
+                pend &= ~(1u << q);
               }
             }
           }
