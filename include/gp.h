@@ -98,17 +98,21 @@ typedef struct gp_config {
   uint32_t batch_indices;     /* static batch size S in indices, a multiple of 3
                                  [warp 96, naive 3*threads, sort/hash/phash 768];
                                  Section 3.3 */
-  uint32_t max_unique;        /* dynamic N: unique indices per batch [256]; Section 3.4 */
-  uint32_t max_tris;          /* dynamic triangle cap per batch [341 = 1023 indices]; Section 4.1 */
-  uint32_t threads_per_group; /* threads per batch for sort/hash/phash [256],
-                                 warps per block for warp [2], block size for naive [256] */
+  uint32_t max_unique;        /* dynamic N: unique indices per batch [256], 3..4096; Section 3.4 */
+  uint32_t max_tris;          /* dynamic triangle cap per batch [341 = 1023 indices], 1..1365;
+                                 Section 4.1.  On GB300 hash/phash draws are fastest at
+                                 max_unique 320, max_tris 426, hash_slots 2048 (one
+                                 producer pass of a 256-thread block per batch) */
+  uint32_t threads_per_group; /* threads per batch for sort/hash/phash, a power of two
+                                 <= 512 [256]; block size for warp voting (one warp per
+                                 batch), a multiple of 32 <= 256 [64]; block size for
+                                 naive and multi, a multiple of 32 <= 256 [256] */
   uint32_t probe_k;           /* parallel hash: per-thread probes before the warp
                                  cooperates [4]; Section 3.4 */
   uint32_t hash_slots;        /* hash table slots, a power of two >= unique capacity and
                                  <= 32768 [the larger of the next power of two >= 2 x
                                  capacity and of min(next power of two >= 4 x capacity,
-                                 1024)]; hash/phash batches hold at most 32 x
-                                 threads_per_group indices */
+                                 1024)] */
   uint32_t segment_tris;      /* dynamic partition: also cut at every multiple of this
                                  many triangles [4096]; GP_SEGMENT_NONE = single scan */
   uint32_t flags;             /* reserved, 0 */
