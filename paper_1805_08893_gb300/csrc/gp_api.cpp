@@ -445,25 +445,27 @@ gp_status enqueue_draw(gp_ctx* c, const gp_index_buf* ib, const gp_vertex_buf* v
   const uint64_t key = (2ull << 56) | ((uint64_t)dedup << 48) | ((uint64_t)dyn << 47) | ((uint64_t)shader << 40) |
                        ((uint64_t)threads << 24) | (uint64_t)smem;  // smem < 2^24
   int bpsm;
+  bool wide = false;
   auto it = c->occ.find(key);
   if (it != c->occ.end()) {
-    bpsm = it->second;
+    bpsm = it->second & 0xFF;
+    wide = (it->second >> 8) != 0;
   } else {
-    bpsm = reuse_blocks_per_sm(dedup, dyn, (int)shader, (int)block, smem);
-    c->occ[key] = bpsm;
+    bpsm = reuse_blocks_per_sm(dedup, dyn, (int)shader, (int)block, smem, &wide);
+    c->occ[key] = bpsm | (wide ? 0x100 : 0);
   }
   if (bpsm <= 0) return fail(c, GP_ERR_UNSUPPORTED, "draw kernel cannot be resident with this configuration");
   uint64_t grid = (uint64_t)c->sms * bpsm;
   if (!dyn) grid = std::min<uint64_t>(grid, a.num_batches);
   if (std::getenv("GP_VERBOSE") && c->logged.insert(key).second)
-    std::fprintf(stderr, "[gp] reuse dedup=%d dyn=%d shader=%u threads=%u smem=%zu blocks/SM=%d grid=%llu slots=%u\n",
-                 dedup, (int)dyn, shader, block, smem, bpsm, (unsigned long long)grid, a.hash_slots);
+    std::fprintf(stderr, "[gp] reuse dedup=%d dyn=%d shader=%u threads=%u smem=%zu blocks/SM=%d grid=%llu slots=%u regs=%d\n",
+                 dedup, (int)dyn, shader, block, smem, bpsm, (unsigned long long)grid, a.hash_slots, wide ? 80 : 64);
   if (c->test_stall_draws) {  // failure injection: this draw's bounded window wait runs out
     --c->test_stall_draws;
     a.test_stall = 1;
   }
   t.device_counts = true;
-  GP_CUDA(c, launch_reuse(dedup, dyn, a, u, (int)shader, (int)block, (int)std::max<uint64_t>(grid, 1), smem,
+  GP_CUDA(c, launch_reuse(dedup, dyn, wide, a, u, (int)shader, (int)block, (int)std::max<uint64_t>(grid, 1), smem,
                           c->stream));
   return GP_OK;
 }

@@ -105,9 +105,11 @@ size_t warp_kernel_smem(int shader, int warps_per_block, uint32_t batch_idx);
 
 // Single-draw sort/hash/phash kernel (gp_reuse.cu).
 size_t reuse_smem_bytes(int dedup, int shader, const DrawArgs& a, int threads);
-cudaError_t launch_reuse(int dedup, bool dynamic, const DrawArgs& a, const Uniforms& u, int shader,
+// Blocks per SM of the 64-register kernel; *wide: the 80-register kernel
+// exists for this draw and fits as many (launch it instead).
+int reuse_blocks_per_sm(int dedup, bool dynamic, int shader, int threads, size_t smem, bool* wide);
+cudaError_t launch_reuse(int dedup, bool dynamic, bool wide, const DrawArgs& a, const Uniforms& u, int shader,
                          int threads, int grid, size_t smem, cudaStream_t s);
-int reuse_blocks_per_sm(int dedup, bool dynamic, int shader, int threads, size_t smem);
 
 size_t partition_smem_bytes(const PartitionArgs& p, int warps);
 cudaError_t launch_partition(const PartitionArgs& p, int warps_per_block, cudaStream_t s);

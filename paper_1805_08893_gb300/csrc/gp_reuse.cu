@@ -175,8 +175,7 @@ struct RowCopy {
 };
 
 template <int DEDUP, int SH, bool DYN>
-__global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ DrawArgs a,
-                                                       const __grid_constant__ Uniforms u) {
+__device__ __forceinline__ void reuse_body(const DrawArgs& a, const Uniforms& u) {
   constexpr int K = ShaderTraits<SH>::K;
   constexpr uint32_t RB = ShaderTraits<SH>::kSkin ? 64u : 32u;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -628,6 +627,24 @@ __global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ D
   }
 }
 
+// The kernel at 64 registers a thread (4 blocks of 256 threads fit an SM's
+// registers) ...
+template <int DEDUP, int SH, bool DYN>
+__global__ void __launch_bounds__(512, 2) reuse_kernel(const __grid_constant__ DrawArgs a,
+                                                       const __grid_constant__ Uniforms u) {
+  reuse_body<DEDUP, SH, DYN>(a, u);
+}
+
+// ... and at up to 80 (3 blocks of 256 threads), for hash/phash draws over
+// dynamic batches with the MVP or envelope shader: where shared memory already
+// holds the block to 3 per SM, the extra registers cost no occupancy and spare
+// the compiler's register-limited scheduling (launch_reuse picks it only then).
+template <int DEDUP, int SH>
+__global__ void __maxnreg__(80) reuse_kernel_wide(const __grid_constant__ DrawArgs a,
+                                                  const __grid_constant__ Uniforms u) {
+  reuse_body<DEDUP, SH, true>(a, u);
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -642,7 +659,15 @@ static const void* reuse_fn_sh(int shader) {
   }
 }
 
-static const void* reuse_kernel_ptr(int dedup, bool dyn, int shader) {
+static const void* reuse_kernel_ptr(int dedup, bool dyn, int shader, bool wide) {
+  if (wide) {  // instantiated for hash/phash, dynamic batches, shaders 0 and 2 only
+    if (dedup == DEDUP_SORT || !dyn || (shader != 0 && shader != 2)) return nullptr;
+    if (dedup == DEDUP_HASH)
+      return shader == 0 ? reinterpret_cast<const void*>(&reuse_kernel_wide<DEDUP_HASH, 0>)
+                         : reinterpret_cast<const void*>(&reuse_kernel_wide<DEDUP_HASH, 2>);
+    return shader == 0 ? reinterpret_cast<const void*>(&reuse_kernel_wide<DEDUP_PHASH, 0>)
+                       : reinterpret_cast<const void*>(&reuse_kernel_wide<DEDUP_PHASH, 2>);
+  }
   if (dyn) {
     switch (dedup) {
       case DEDUP_SORT: return reuse_fn_sh<DEDUP_SORT, true>(shader);
@@ -661,8 +686,8 @@ size_t reuse_smem_bytes(int dedup, int shader, const DrawArgs& a, int threads) {
   return reuse_layout(dedup, shader, a, (uint32_t)threads).total;
 }
 
-int reuse_blocks_per_sm(int dedup, bool dynamic, int shader, int threads, size_t smem) {
-  const void* fn = reuse_kernel_ptr(dedup, dynamic, shader);
+static int blocks_per_sm(const void* fn, int threads, size_t smem) {
+  if (fn == nullptr) return 0;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   int nb = 0;
@@ -670,9 +695,17 @@ int reuse_blocks_per_sm(int dedup, bool dynamic, int shader, int threads, size_t
   return nb;
 }
 
-cudaError_t launch_reuse(int dedup, bool dynamic, const DrawArgs& a, const Uniforms& u, int shader, int threads,
-                         int grid, size_t smem, cudaStream_t s) {
-  const void* fn = reuse_kernel_ptr(dedup, dynamic, shader);
+int reuse_blocks_per_sm(int dedup, bool dynamic, int shader, int threads, size_t smem, bool* wide) {
+  const int nb = blocks_per_sm(reuse_kernel_ptr(dedup, dynamic, shader, false), threads, smem);
+  // the 80-register kernel where it exists and fits as many blocks per SM
+  *wide = nb > 0 && blocks_per_sm(reuse_kernel_ptr(dedup, dynamic, shader, true), threads, smem) == nb;
+  return nb;
+}
+
+cudaError_t launch_reuse(int dedup, bool dynamic, bool wide, const DrawArgs& a, const Uniforms& u, int shader,
+                         int threads, int grid, size_t smem, cudaStream_t s) {
+  const void* fn = reuse_kernel_ptr(dedup, dynamic, shader, wide);
+  if (fn == nullptr) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
